@@ -1,0 +1,226 @@
+"""Pins of the oracle's whole time step against results the paper or the
+mathematics fixes: fixed points, closed-form transients, conservation, the
+Laplace law, the layered-Poiseuille solution (Eq. 31, Table 1), checkpoint
+resume, and brute force against an independent NumPy transcription.
+
+Each test names the mistake it would catch."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_09541_gb300 import cases
+from tests import brute_numpy as bn
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _lattice(nx, ny, **kw):
+    return oracle.Lattice(nx, ny, **kw)
+
+
+def test_uniform_state_is_a_fixed_point():
+    """Uniform phi, u, p with no gradients is stationary; u and p read back
+    exactly (catches a dropped rho*s_0 in Eq. 22b or a wrong g_0^eq)."""
+    nx, ny = 9, 7
+    phi = np.full((ny, nx), 0.3)
+    ux, uy, p = np.full_like(phi, 0.01), np.full_like(phi, -0.02), np.full_like(phi, 1e-3)
+    lat = _lattice(nx, ny, sigma=0.01).init(phi, ux, uy, p)
+    lat.step(50)
+    F = lat.fields()
+    assert np.allclose(F["phi"], 0.3, rtol=1e-14, atol=0)
+    assert np.allclose(F["ux"], 0.01, rtol=1e-12, atol=0)
+    assert np.allclose(F["uy"], -0.02, rtol=1e-12, atol=0)
+    assert np.allclose(F["p"], 1e-3, rtol=1e-11, atol=0)
+
+
+def test_uniform_body_force_closed_form():
+    """Uniform fluid under a constant body force G (Eq. 4b): the half-force
+    velocity of Eq. 22a and the first moment of G_i (Eq. A2) give
+    rho u(t) = G (t + 1/2) exactly (catches a missing F/2 or a wrong force
+    moment)."""
+    nx, ny = 6, 5
+    G = np.array([1e-6, -2e-6])
+    lat = _lattice(nx, ny, rho_l=1.0, rho_g=1.0, Gx=G[0], Gy=G[1]).init(np.ones((ny, nx)))
+    for t in range(0, 60, 7):
+        F = lat.fields()
+        assert np.allclose(F["rho"] * F["ux"], G[0] * (t + 0.5), rtol=1e-10, atol=0)
+        assert np.allclose(F["rho"] * F["uy"], G[1] * (t + 0.5), rtol=1e-10, atol=0)
+        lat.step(7)
+
+
+def _shear_wave_rate(mode, phi_val):
+    nx, ny = 4, 64
+    # sigma = 0 removes the chemical potential; a very wide W makes lambda of
+    # Eq. 3 vanish, so the uniform mixed phi is not driven apart by Eq. 1's
+    # sharpening flux and the flow sees one constant viscosity
+    P = dict(rho_l=1.0, rho_g=0.05, nu_l=0.08, nu_g=0.2, visc_mode=mode, sigma=0.0, W=1e12)
+    k = 2 * np.pi / ny
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    u0 = 1e-4 * np.sin(k * y)
+    lat = _lattice(nx, ny, **P).init(np.full((ny, nx), phi_val), u0)
+    lat.step(100)
+    a1 = (lat.fields()["ux"][:, 0] * np.sin(k * np.arange(ny))).sum()
+    lat.step(400)
+    F = lat.fields()
+    assert np.abs(F["phi"] - phi_val).max() < 1e-8  # O(u^2) with u = 1e-4
+    a2 = (F["ux"][:, 0] * np.sin(k * np.arange(ny))).sum()
+    rate = np.log(a1 / a2) / 400
+    return rate, k, oracle.viscosity(oracle.make_params(**P), phi_val)
+
+
+@pytest.mark.parametrize("mode,phi_val", [(0, 0.3), (1, 0.3), (2, 0.3), (2, 0.7)])
+def test_shear_wave_decay_matches_viscosity(mode, phi_val):
+    """A shear wave decays as exp(-nu k_d^2 t) with k_d^2 = 2(1 - cos k), the
+    lattice Laplacian's eigenvalue; nu = c_s^2 (tau_g - 1/2) (Eq. 23) with nu
+    from Eq. 24, 25 or 26 (catches a wrong tau_g or viscosity rule)."""
+    rate, k, nu = _shear_wave_rate(mode, phi_val)
+    assert abs(rate / (nu * 2 * (1 - np.cos(k))) - 1) < 0.01
+
+
+def test_drop_translates_with_uniform_flow():
+    """Without surface tension and with equal densities, u stays uniform and
+    the conservative Allen-Cahn equation (Eq. 1) carries the drop's centroid at
+    exactly u (catches a reversed streaming direction, a wrong sign in Eq. 9 or
+    a transposed axis)."""
+    nx = ny = 48
+    U = np.array([0.02, 0.01])
+    phi0 = cases.drop(nx, ny, 8, 4.0, x0=16.0, y0=16.0)
+    lat = _lattice(nx, ny, rho_l=1.0, rho_g=1.0, sigma=0.0, W=4.0).init(
+        phi0, np.full_like(phi0, U[0]), np.full_like(phi0, U[1]))
+    T = 400
+    lat.step(T)
+    phi = lat.fields()["phi"]
+    y, x = np.mgrid[0:ny, 0:nx]
+    c0 = np.array([(x * phi0).sum(), (y * phi0).sum()]) / phi0.sum()
+    c1 = np.array([(x * phi).sum(), (y * phi).sum()]) / phi.sum()
+    assert np.allclose(c1 - c0, U * T, atol=0.05)
+    # the drop keeps its shape: the interface stays sharp (Eqs. 1-3)
+    assert phi.max() > 0.99 and phi.min() > -0.01
+
+
+@pytest.mark.parametrize("bc_y", [0, 1])
+def test_phi_is_conserved(bc_y):
+    """Collision conserves sum f_i (sum F_i = 0), streaming and half-way
+    bounce-back permute: sum phi is constant to round-off (catches a lost or
+    duplicated population at a wall)."""
+    nx, ny = 40, 36
+    phi0 = cases.drop(nx, ny, 10, 4.0, x0=20.0, y0=11.0, walls_y=bool(bc_y))
+    u0 = 1e-3 * np.sin(np.arange(nx) / 5.0)[None, :] * np.ones((ny, 1))
+    lat = _lattice(nx, ny, rho_g=0.01, bc_y=bc_y, Gx=1e-6, Gy=-1e-6).init(phi0, u0, -u0)
+    s0 = lat.sum_phi()
+    lat.step(2000)
+    assert abs(lat.sum_phi() - s0) / s0 < 1e-12
+
+
+def test_laplace_law():
+    """Static drop (64 x 64, R = 16, sigma = 0.01, ratio 1000): the pressure
+    jump settles at sigma/R (Laplace law); time-averaged over the decaying
+    acoustic oscillation (catches wrong k, beta of Eq. 7 or a wrong sign in
+    Eq. 6)."""
+    nx = ny = 64
+    P = cases.params_static_drop()
+    lat = _lattice(nx, ny, **P).init(cases.drop(nx, ny, 16, 4.0))
+    lat.step(5000)
+    dps = []
+    for _ in range(40):
+        lat.step(125)
+        F = lat.fields()
+        dps.append(F["p"][32, 32] - F["p"][0, 0])
+    assert abs(np.mean(dps) / (0.01 / 16) - 1) < 0.03
+
+
+def _poiseuille(ny, nx, params, steps, u_start):
+    lat = _lattice(nx, ny, **params).init(cases.layer(nx, ny, params["W"]),
+                                          np.broadcast_to(u_start[:, None], (ny, nx)))
+    lat.step(steps)
+    return lat.fields()["ux"][:, nx // 2]
+
+
+def _two_layer_profile(ny, P):
+    """Eq. 31 at node centres y_j = j + 1/2 - ny/2, h = ny/2, liquid below."""
+    h = ny / 2.0
+    s = (np.arange(ny) + 0.5 - h) / h
+    mu_l, mu_g, G = P["rho_l"] * P["nu_l"], P["rho_g"] * P["nu_g"], P["Gx"]
+    a = (mu_g - mu_l) / (mu_g + mu_l)
+    up = G * h * h / (2 * mu_g) * (-s ** 2 - s * a + 2 * mu_g / (mu_g + mu_l))
+    lo = G * h * h / (2 * mu_l) * (-s ** 2 - s * a + 2 * mu_l / (mu_g + mu_l))
+    return np.where(s > 0, up, lo)
+
+
+def test_single_phase_poiseuille():
+    """Equal phases between half-way bounce-back walls: the steady profile is
+    the parabola G y (H - y) / (2 mu) (catches a wrong wall rule or viscosity)."""
+    ny, nx = 32, 4
+    P = dict(rho_l=1.0, rho_g=1.0, nu_l=0.1, nu_g=0.1, sigma=0.0, W=4.0, Gx=1e-6, bc_y=1)
+    y = np.arange(ny) + 0.5
+    exact = 1e-6 * y * (ny - y) / (2 * 0.1)
+    u = _poiseuille(ny, nx, P, 20000, np.zeros(ny))
+    assert np.sqrt(((u - exact) ** 2).sum() / (exact ** 2).sum()) < 2e-3
+
+
+def test_layered_poiseuille_table1_ratio10():
+    """Layered Poiseuille flow at the paper's setup (100 x 10 -> 100 x 4, the
+    flow is x-uniform), density ratio 10, step viscosity (Eq. 26).  Table 1
+    prints E_u = 8.9e-3; this oracle (central-gradient normal, node centres
+    half a cell from the walls) reaches 1.5e-2.  The bound 2.5x the printed
+    value still fails for a missing Lambda term of Eq. 20 (E_u ~ 2), a wrong
+    interface side or a wrong viscosity rule."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "table1_poiseuille_Eu.txt"))
+    ratio, nu_ratio, Eu_paper = rows[0]
+    ny, nx = 100, 4
+    rho_l, nu_l, uc, h = 1.0, 0.1, 1e-4, 50.0
+    rho_g = rho_l / ratio
+    nu_g = nu_ratio * nu_l
+    G = uc * (rho_l * nu_l + rho_g * nu_g) / h ** 2
+    P = dict(rho_l=rho_l, rho_g=rho_g, nu_l=nu_l, nu_g=nu_g, visc_mode=2, sigma=1e-3, W=5.0,
+             tau_h=0.8, Gx=G, bc_y=1)
+    ua = _two_layer_profile(ny, P)
+    u = _poiseuille(ny, nx, P, 60000, ua)
+    Eu = np.abs(u - ua).sum() / np.abs(ua).sum()   # Eq. 32
+    assert Eu < 2.5 * Eu_paper
+    assert u[:ny // 2].max() < u[ny // 2:].max()   # the gas layer (upper) moves faster
+
+
+@pytest.mark.parametrize("bc_y", [0, 1])
+def test_brute_force_numpy_transcription(bc_y):
+    """8 x 8 grids, 10 steps, against the independent whole-array NumPy
+    transcription (catches index and sign slips in either)."""
+    nx = ny = 8
+    r = np.random.default_rng(7 + bc_y)
+    phi0 = cases.drop(nx, ny, 2.5, 3.0, x0=3.7, y0=4.2, walls_y=bool(bc_y)) + 0.01 * r.random((ny, nx))
+    ux0 = 0.01 * r.standard_normal((ny, nx))
+    uy0 = 0.01 * r.standard_normal((ny, nx))
+    p0 = 1e-4 * r.standard_normal((ny, nx))
+    P = dict(rho_l=1.0, rho_g=0.01, nu_l=0.05, nu_g=0.2, visc_mode=bc_y + 1 if bc_y else 0,
+             sigma=0.02, W=3.0, tau_h=0.9, Gx=1e-5, Gy=-2e-5, bc_y=bc_y)
+    lat = _lattice(nx, ny, **P).init(phi0, ux0, uy0, p0)
+    f, g, phiu = bn.init(phi0, ux0, uy0, p0, P)
+    of, og, ophiu = lat.get_state()
+    assert np.allclose(of, f, atol=1e-16) and np.allclose(og, g, atol=1e-17)
+    for _ in range(10):
+        f, g, phiu = bn.step(f, g, phiu, P)
+    lat.step(10)
+    of, og, ophiu = lat.get_state()
+    assert np.abs(of - f).max() < 1e-13
+    assert np.abs(og - g).max() < 1e-15
+    assert np.abs(ophiu - phiu).max() < 1e-15
+    m = bn.moments(f, g, P, bool(bc_y))
+    F = lat.fields()
+    for k in ("phi", "ux", "uy", "p", "mu"):
+        assert np.abs(F[k] - m[k]).max() <= 1e-12 * max(1.0, np.abs(m[k]).max()), k
+
+
+def test_checkpoint_resume_is_exact():
+    nx, ny = 20, 16
+    P = cases.params_static_drop()
+    phi0 = cases.drop(nx, ny, 5, 4.0)
+    a = _lattice(nx, ny, **P).init(phi0)
+    a.step(30)
+    b = _lattice(nx, ny, **P).init(phi0)
+    b.step(12)
+    c = _lattice(nx, ny, **P).set_state(*b.get_state())
+    c.step(18)
+    for x, y in zip(a.get_state(), c.get_state()):
+        assert np.array_equal(x, y)
