@@ -1,0 +1,155 @@
+/*
+ * lbm_pf.h -- C ABI of the GB300 (sm_103a) phase-field lattice Boltzmann
+ * library: the per-time-step lattice update of the two-distribution model of
+ * Liang, Xu, Chen, Wang, Chai & Shi, "Phase-field-based lattice Boltzmann
+ * modeling of large-density-ratio two-phase flows" (arXiv:1710.09541, 2018),
+ * Sec. II, on a D2Q9 grid.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grid: nx * ny nodes, node (x, y) at linear index y*nx + x (x fastest).
+ *    Lattice units: dx = dt = 1, c_s^2 = 1/3 (Eq. 10).
+ *  - x is always periodic.  y is periodic (bc_y = LBM_BC_PERIODIC) or closed
+ *    by half-way bounce-back walls at y = -1/2 and y = ny - 1/2
+ *    (LBM_BC_WALLS; Sec. III B and III D).
+ *  - Host arrays passed in or out are double precision, N = nx*ny entries,
+ *    owned by the caller; the library copies them and keeps no pointer.
+ *  - All device memory is owned by the handle: allocated by lbm_create,
+ *    released by lbm_destroy.  All GPU work is enqueued on params.stream
+ *    (NULL = the legacy default stream).
+ *  - Every call returns an lbm_status; nothing aborts, traps or exits.  After
+ *    a failure lbm_last_error(h) returns a one-line description.
+ *  - A handle is not thread-safe: one host thread per handle.
+ *  - Arithmetic on the device is IEEE FP32 (no fast-math); diagnostics that
+ *    sum over the grid accumulate in FP64.
+ */
+#ifndef LBM_PF_H
+#define LBM_PF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_handle lbm_handle;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID = -1,   /* bad argument or parameter set */
+    LBM_ERR_CUDA = -2,      /* a CUDA runtime call failed (message kept) */
+    LBM_ERR_STATE = -3,     /* step/get called before lbm_init */
+    LBM_ERR_NONFINITE = -4, /* a NaN/Inf appeared in phi, u or p */
+    LBM_ERR_OOM = -5        /* device or host allocation failed */
+} lbm_status;
+
+/* viscosity rule across the interface (visc_mode) */
+enum {
+    LBM_VISC_LINEAR_NU = 0,  /* nu = phi (nu_l - nu_g) + nu_g            Eq. 24 */
+    LBM_VISC_INVERSE_NU = 1, /* 1/nu = phi (1/nu_l - 1/nu_g) + 1/nu_g     Eq. 25 */
+    LBM_VISC_STEP_MU = 2     /* mu = rho_l nu_l if phi >= 1/2 else rho_g nu_g,
+                                nu = mu / rho(phi)                        Eq. 26 */
+};
+enum { LBM_BC_PERIODIC = 0, LBM_BC_WALLS = 1 };
+/* unit normal n of the sharpening term (normal_scheme) */
+enum {
+    LBM_NORMAL_CENTRAL = 0, /* n = grad phi / |grad phi|, grad by Eq. 27  (Eq. 2) */
+    LBM_NORMAL_LOCAL = 1    /* n from the non-equilibrium of f_i           (Eq. 29) */
+};
+enum { LBM_STORE_FP32 = 0 };
+
+typedef struct {
+    double rho_l, rho_g;  /* liquid / gas densities, Eq. 13; rho_g > 0 */
+    double nu_l, nu_g;    /* kinematic viscosities of the pure phases, Eqs. 24-26; > 0 */
+    int visc_mode;        /* LBM_VISC_* */
+    double sigma;         /* surface tension; k = 3 sigma W / 2, beta = 12 sigma / W (Eq. 7); >= 0 */
+    double W;             /* interface thickness, Eqs. 3 and 7; > 0 */
+    double tau_h;         /* Allen-Cahn relaxation time (tau_f of Eq. 8); > 1/2;
+                             mobility M = (tau_h - 1/2)/3 (Eq. 14) */
+    double Gx, Gy;        /* body-force density G (Eqs. 4b, 19), same in both phases */
+    int bc_y;             /* LBM_BC_PERIODIC or LBM_BC_WALLS */
+    int normal_scheme;    /* LBM_NORMAL_* */
+    int storage;          /* LBM_STORE_FP32 (populations stored as FP32) */
+    int check_every;      /* > 0: every check_every steps lbm_step synchronises the
+                             stream and returns LBM_ERR_NONFINITE if any node produced
+                             a non-finite phi, u or p since the last check; 0: off */
+    void* stream;         /* cudaStream_t for all work; NULL = default stream */
+} lbm_params;
+
+/*
+ * lbm_create -- validate the parameters and allocate the device state for an
+ * nx x ny grid: two buffers of 9 FP32 planes for each of f_i (Allen-Cahn,
+ * Eq. 8) and g_i (Navier-Stokes, Eq. 15), two FP32 planes holding (phi u) of
+ * the previous step (for d_t(phi u) in Eq. 11), and staging for host I/O.
+ * Requires nx >= 1, ny >= 1 (ny >= 2 with walls), nx*ny < 2^31, and the
+ * parameter ranges listed in lbm_params.  On success *out owns everything.
+ * Errors: LBM_ERR_INVALID, LBM_ERR_OOM, LBM_ERR_CUDA (then *out == NULL).
+ */
+lbm_status lbm_create(int nx, int ny, const lbm_params* p, lbm_handle** out);
+
+/*
+ * lbm_init -- set the state to equilibrium: f_i = f_i^eq(phi0, u0) (Eq. 9),
+ * g_i = g_i^eq(p0, rho(phi0), u0) (Eqs. 13, 16, 17), and the previous-step
+ * (phi u) to phi0 * u0.  phi0 is required; ux0, uy0, p0 may be NULL (= 0).
+ * Host arrays of N doubles.  Enqueued on the stream; the host arrays may be
+ * reused when the call returns (the copies are synchronous to the host).
+ */
+lbm_status lbm_init(lbm_handle* h, const double* phi0, const double* ux0,
+                    const double* uy0, const double* p0);
+
+/*
+ * lbm_step -- advance nsteps >= 0 time steps.  One step is, per node: stream
+ * f_i and g_i (pull; Eqs. 8, 15 left-hand sides) with periodic or half-way
+ * bounce-back links; phi = sum f_i (Eq. 12); rho (Eq. 13); grad phi and
+ * lap phi (Eqs. 27, 28); mu_phi (Eqs. 6, 7); F = mu_phi grad phi + G
+ * (Eqs. 5, 19); u and p (Eq. 22); tau_g from nu (Eqs. 23-26); the Allen-Cahn
+ * collision with source F_i (Eqs. 2, 3, 8, 9, 11; d_t(phi u) as the backward
+ * difference over one step); the Navier-Stokes collision with forcing G_i
+ * (Eqs. 15-17, 20).  Asynchronous on the stream unless check_every triggers
+ * a check.  Errors: LBM_ERR_STATE (no init), LBM_ERR_NONFINITE, LBM_ERR_CUDA.
+ */
+lbm_status lbm_step(lbm_handle* h, int nsteps);
+
+/*
+ * lbm_get_fields -- phi, rho, ux, uy, p of the current state, computed by the
+ * same formulas as the step (Eqs. 12, 13, 22).  Any output may be NULL.
+ * Host arrays of N doubles; synchronises the stream before returning.
+ */
+lbm_status lbm_get_fields(lbm_handle* h, double* phi, double* rho, double* ux,
+                          double* uy, double* p);
+
+/*
+ * lbm_state_bytes -- size of the checkpoint: 20 * N * sizeof(float).
+ * lbm_get_state / lbm_set_state -- copy the complete state to / from a host
+ * buffer of exactly that size, laid out as FP32 f[9][ny][nx], g[9][ny][nx]
+ * (pre-collision populations of the current time, i.e. after streaming,
+ * velocity index i in the order of Eq. 10), then (phi u_x, phi u_y) of the
+ * previous step [2][ny][nx].  Restoring a saved state and stepping reproduces
+ * the uninterrupted run bit for bit.  Both synchronise the stream.
+ */
+size_t lbm_state_bytes(const lbm_handle* h);
+lbm_status lbm_get_state(lbm_handle* h, void* host_buf, size_t bytes);
+lbm_status lbm_set_state(lbm_handle* h, const void* host_buf, size_t bytes);
+
+/*
+ * lbm_diag -- grid reductions of the current state: sum of phi (FP64
+ * accumulation; conserved by the scheme, Eqs. 8-12), max |u|, min p, max p.
+ * Any output may be NULL.  Synchronises the stream.
+ */
+lbm_status lbm_diag(lbm_handle* h, double* sum_phi, double* umax, double* pmin,
+                    double* pmax);
+
+/* lbm_synchronize -- wait for all work enqueued by this handle. */
+lbm_status lbm_synchronize(lbm_handle* h);
+
+/* lbm_destroy -- free everything the handle owns; NULL is a no-op. */
+void lbm_destroy(lbm_handle* h);
+
+/* lbm_last_error -- description of the last failure on h (never NULL). */
+const char* lbm_last_error(const lbm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_PF_H */

@@ -27,7 +27,10 @@
  *   - Eq. 27 prints c_k inside a sum over i: read c_i.
  *   - d_t(phi u) in Eq. 11 is the first-order backward difference
  *     (phi u)^t - (phi u)^{t-1}; the history starts as phi0*u0.
- *   - n = grad phi / |grad phi| when |grad phi| > 1e-12, else n = 0.
+ *   - n = grad phi / |grad phi| when |grad phi| > 1e-6, else n = 0.  Where
+ *     grad phi vanishes (a symmetry point, a far tail) n is 0/0; the cut-off
+ *     sits above the round-off of an FP32 stencil of an O(1) field (~1e-7)
+ *     so single- and double-precision evaluations take the same branch.
  *   - At a half-way bounce-back wall the phi stencil uses a mirror ghost
  *     phi(y=-1) = phi(0), phi(ny) = phi(ny-1) (neutral wall).
  *   - The step-function viscosity of Eq. 26 takes the liquid value at
@@ -164,6 +167,7 @@ static double phi_at(const double* phi, int nx, int ny, int bc_y, int x, int y) 
  * lap phi  = sum_{i!=0} 2 w_i [phi(x + c_i) - phi(x)] / c_s^2       (Eq. 28) */
 void orc_grad_lap(int nx, int ny, int bc_y, const double* phi,
                   double* gpx, double* gpy, double* lap) {
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             double c = phi[(size_t)y * nx + x];
@@ -248,7 +252,8 @@ int orc_init(orc_lattice* L, const double* phi0, const double* ux0,
 /* phi over the whole grid (Eq. 12) and its stencils (Eqs. 27, 28) */
 static void order_parameter_and_stencils(orc_lattice* L) {
     size_t N = (size_t)L->nx * L->ny;
-    for (size_t n = 0; n < N; ++n) {
+#pragma omp parallel for schedule(static)
+    for (long long n = 0; n < (long long)N; ++n) {
         double s = 0.0;
         for (int i = 0; i < 9; ++i) s += L->f[i * N + n];
         L->phi[n] = s;
@@ -299,7 +304,7 @@ static void unit_normal(const orc_lattice* L, size_t n, const double* fpre,
     if (L->p.normal_scheme == 0) {
         double gx = L->gpx[n], gy = L->gpy[n];
         double mag = sqrt(gx * gx + gy * gy);
-        if (mag > 1e-12) {
+        if (mag > 1e-6) {
             *nx_o = gx / mag;
             *ny_o = gy / mag;
         } else {
@@ -317,7 +322,7 @@ static void unit_normal(const orc_lattice* L, size_t n, const double* fpre,
         Cy += CY[i] * (fpre[i] - feq[i]);
     }
     double mag = sqrt(Cx * Cx + Cy * Cy);
-    if (mag > 1e-12) {
+    if (mag > 1e-6) {
         *nx_o = -Cx / mag;
         *ny_o = -Cy / mag;
     } else {
@@ -409,7 +414,8 @@ int orc_get_fields(orc_lattice* L, double* phi, double* rho, double* ux,
                    double* uy, double* p, double* mu) {
     size_t N = (size_t)L->nx * L->ny;
     order_parameter_and_stencils(L);
-    for (size_t n = 0; n < N; ++n) {
+#pragma omp parallel for schedule(static)
+    for (long long n = 0; n < (long long)N; ++n) {
         double r, m, Fx, Fy, vx, vy, pp;
         macroscopic(L, n, &r, &m, &Fx, &Fy, &vx, &vy, &pp);
         if (phi) phi[n] = L->phi[n];

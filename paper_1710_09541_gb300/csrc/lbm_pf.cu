@@ -1,0 +1,600 @@
+// lbm_pf.cu -- kernels and C ABI (include/lbm_pf.h) of the GB300 phase-field
+// lattice Boltzmann library (Liang et al., arXiv:1710.09541, Sec. II).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "lbm_kernels.cuh"
+#include "lbm_pf.h"
+
+using namespace lbmpf;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// The fused step kernel.  One thread per node of a TX x TY tile.  Phase 1
+// pulls f_i and g_i of the node, forms phi (Eq. 12) and writes it to shared
+// memory; threads also form phi on the one-node ring around the tile (each
+// ring node pulls its own 9 f_i, mostly L2 hits as neighbouring tiles read
+// the same lines).  Phase 2 takes the stencils of Eqs. 27-28 from shared
+// memory, recovers rho, mu_phi, F, u, p (Eqs. 5-7, 13, 19, 22), collides f and
+// g (Eqs. 8-11, 15-20) and stores both sets at the node's own address.
+//
+// FIELDS = true evaluates the same formulas but writes phi, rho, ux, uy, p
+// as doubles instead of colliding (used by lbm_get_fields and lbm_diag).
+// ---------------------------------------------------------------------------
+template <int TX, int TY>
+struct Ring {
+    static constexpr int count = 2 * (TX + 2) + 2 * TY;
+    __device__ static void pos(int r, int& lx, int& ly) {
+        if (r < TX + 2) {
+            lx = r - 1;
+            ly = -1;
+        } else if (r < 2 * (TX + 2)) {
+            lx = r - (TX + 2) - 1;
+            ly = TY;
+        } else if (r < 2 * (TX + 2) + TY) {
+            lx = -1;
+            ly = r - 2 * (TX + 2);
+        } else {
+            lx = TX;
+            ly = r - 2 * (TX + 2) - TY;
+        }
+    }
+};
+
+template <int TX, int TY, bool FIELDS>
+__global__ void __launch_bounds__(TX* TY)
+    k_step(const float* __restrict__ fs, const float* __restrict__ gs, float* __restrict__ fd,
+           float* __restrict__ gd, float* __restrict__ phiu, unsigned int* __restrict__ flag,
+           double* __restrict__ out, int nx, int ny, Model m) {
+    __shared__ float sphi[TY + 2][TX + 2];
+    const size_t N = (size_t)nx * ny;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = (x < nx) && (y < ny);
+
+    float f[9], g[9];
+    Nbr q;
+    if (active) {
+        q = make_nbr(x, y, nx, ny, m.walls);
+        pull9(fs, N, q, f);
+        pull9(gs, N, q, g);
+        sphi[ty + 1][tx + 1] = sum9(f);
+    } else {
+        sphi[ty + 1][tx + 1] = phi_at(fs, N, fold_x(x, nx), fold_y(y, ny, m.walls), nx, ny, m.walls);
+    }
+    for (int r = ty * TX + tx; r < Ring<TX, TY>::count; r += TX * TY) {
+        int lx, ly;
+        Ring<TX, TY>::pos(r, lx, ly);
+        sphi[ly + 1][lx + 1] =
+            phi_at(fs, N, fold_x(x0 + lx, nx), fold_y(y0 + ly, ny, m.walls), nx, ny, m.walls);
+    }
+    __syncthreads();
+    if (!active) return;
+
+    const int lx = tx + 1, ly = ty + 1;
+    const float phi = sphi[ly][lx];
+    const Stencil st = stencil(phi, sphi[ly][lx + 1], sphi[ly][lx - 1], sphi[ly + 1][lx],
+                               sphi[ly - 1][lx], sphi[ly + 1][lx + 1], sphi[ly + 1][lx - 1],
+                               sphi[ly - 1][lx - 1], sphi[ly - 1][lx + 1]);
+    const Macro M = macroscopic(m, g, phi, st.gx, st.gy, st.lap);
+    const size_t n = (size_t)q.r0 + x;
+
+    if (FIELDS) {
+        out[n] = phi;
+        out[N + n] = M.rho;
+        out[2 * N + n] = M.ux;
+        out[3 * N + n] = M.uy;
+        out[4 * N + n] = M.p;
+        return;
+    }
+    if (!(isfinite(phi) && isfinite(M.ux) && isfinite(M.uy) && isfinite(M.p))) atomicOr(flag, 1u);
+
+    const float2 prev = make_float2(phiu[n], phiu[N + n]);
+    const float2 now = collide(m, f, g, phi, st, M, prev);
+    phiu[n] = now.x;
+    phiu[N + n] = now.y;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        fd[i * N + n] = f[i];
+        gd[i * N + n] = g[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initial state.  The canonical (pre-collision) state is f_i = f_i^eq(phi0,u0)
+// (Eq. 9) and g_i = g_i^eq(p0, rho(phi0), u0) (Eqs. 13, 16, 17).  The pull
+// buffer must hold values that stream into it, so each entry B_j(z) takes the
+// equilibrium of node z + c_j; where z + c_j lies beyond a wall, the link is
+// the bounce-back one and B_j(z) holds the opposite direction's value at z.
+// in = [phi0 | ux0 | uy0 | p0] as doubles (N each).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void eq_at(const double* __restrict__ in, size_t N, size_t s, int i,
+                                      const Model& m, float& fe, float& ge) {
+    const float phi = (float)in[s];
+    const float ux = (float)in[N + s], uy = (float)in[2 * N + s], p = (float)in[3 * N + s];
+    const float rho = fmaf(phi, m.drho, m.rho_g);
+    const float w = w_of(i);
+    const float cu = cx_of(i) * ux + cy_of(i) * uy;
+    const float usq = ux * ux + uy * uy;
+    const float wphi = w * phi;
+    fe = fmaf(3.f * wphi, cu, wphi);
+    const float s_i = w * (cu * fmaf(4.5f, cu, 3.f) - 1.5f * usq);
+    ge = (i == 0 ? 3.f * p * (w - 1.f) : 3.f * p * w) + rho * s_i;
+}
+
+__global__ void k_init(const double* __restrict__ in, float* __restrict__ fd,
+                       float* __restrict__ gd, float* __restrict__ phiu, int nx, int ny, Model m) {
+    const size_t N = (size_t)nx * ny;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(n % nx), y = (int)(n / nx);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const int yy = y + cy_of(j);
+            float fe, ge;
+            if (m.walls && (yy < 0 || yy >= ny)) {
+                eq_at(in, N, n, opp_of(j), m, fe, ge);
+            } else {
+                const int xs = fold_x(x + cx_of(j), nx), ys = fold_y(yy, ny, 0);
+                eq_at(in, N, (size_t)ys * nx + xs, j, m, fe, ge);
+            }
+            fd[j * N + n] = fe;
+            gd[j * N + n] = ge;
+        }
+        const float phi = (float)in[n];
+        phiu[n] = phi * (float)in[N + n];
+        phiu[N + n] = phi * (float)in[2 * N + n];
+    }
+}
+
+// Checkpoint out: canonical pre-collision state = the pulled populations.
+__global__ void k_state_out(const float* __restrict__ fs, const float* __restrict__ gs,
+                            const float* __restrict__ phiu, float* __restrict__ st, int nx,
+                            int ny, int walls) {
+    const size_t N = (size_t)nx * ny;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(n % nx), y = (int)(n / nx);
+        const Nbr q = make_nbr(x, y, nx, ny, walls);
+        float v[9];
+        pull9(fs, N, q, v);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st[i * N + n] = v[i];
+        pull9(gs, N, q, v);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st[(9 + i) * N + n] = v[i];
+        st[18 * N + n] = phiu[n];
+        st[19 * N + n] = phiu[N + n];
+    }
+}
+
+// Checkpoint in: the inverse permutation of the pull (see k_init).
+__global__ void k_state_in(const float* __restrict__ st, float* __restrict__ fd,
+                           float* __restrict__ gd, float* __restrict__ phiu, int nx, int ny,
+                           int walls) {
+    const size_t N = (size_t)nx * ny;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(n % nx), y = (int)(n / nx);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const int yy = y + cy_of(j);
+            size_t src;
+            int dir;
+            if (walls && (yy < 0 || yy >= ny)) {
+                src = n;
+                dir = opp_of(j);
+            } else {
+                src = (size_t)fold_y(yy, ny, 0) * nx + fold_x(x + cx_of(j), nx);
+                dir = j;
+            }
+            fd[j * N + n] = st[dir * N + src];
+            gd[j * N + n] = st[(9 + dir) * N + src];
+        }
+        phiu[n] = st[18 * N + n];
+        phiu[N + n] = st[19 * N + n];
+    }
+}
+
+// Grid reductions over the fields buffer [phi|rho|ux|uy|p] (doubles):
+// block partials (sum phi, max |u|, min p, max p) into scratch, then one block
+// folds the partials in a fixed order.
+constexpr int RED_THREADS = 256;
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_diag_partial(const double* __restrict__ fields, size_t N, double* __restrict__ part) {
+    __shared__ double s_sum[RED_THREADS], s_um[RED_THREADS], s_pmin[RED_THREADS],
+        s_pmax[RED_THREADS];
+    double sum = 0.0, um = 0.0, pmin = INFINITY, pmax = -INFINITY;
+    for (size_t n = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * RED_THREADS) {
+        sum += fields[n];
+        const double ux = fields[2 * N + n], uy = fields[3 * N + n], p = fields[4 * N + n];
+        um = fmax(um, sqrt(ux * ux + uy * uy));
+        pmin = fmin(pmin, p);
+        pmax = fmax(pmax, p);
+    }
+    const int t = threadIdx.x;
+    s_sum[t] = sum;
+    s_um[t] = um;
+    s_pmin[t] = pmin;
+    s_pmax[t] = pmax;
+    __syncthreads();
+    for (int h = RED_THREADS / 2; h > 0; h >>= 1) {
+        if (t < h) {
+            s_sum[t] += s_sum[t + h];
+            s_um[t] = fmax(s_um[t], s_um[t + h]);
+            s_pmin[t] = fmin(s_pmin[t], s_pmin[t + h]);
+            s_pmax[t] = fmax(s_pmax[t], s_pmax[t + h]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        part[4 * blockIdx.x + 0] = s_sum[0];
+        part[4 * blockIdx.x + 1] = s_um[0];
+        part[4 * blockIdx.x + 2] = s_pmin[0];
+        part[4 * blockIdx.x + 3] = s_pmax[0];
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_diag_final(const double* __restrict__ part, int nb, double* __restrict__ res) {
+    __shared__ double s_sum[RED_THREADS], s_um[RED_THREADS], s_pmin[RED_THREADS],
+        s_pmax[RED_THREADS];
+    const int t = threadIdx.x;
+    double sum = 0.0, um = 0.0, pmin = INFINITY, pmax = -INFINITY;
+    for (int b = t; b < nb; b += RED_THREADS) {
+        sum += part[4 * b];
+        um = fmax(um, part[4 * b + 1]);
+        pmin = fmin(pmin, part[4 * b + 2]);
+        pmax = fmax(pmax, part[4 * b + 3]);
+    }
+    s_sum[t] = sum;
+    s_um[t] = um;
+    s_pmin[t] = pmin;
+    s_pmax[t] = pmax;
+    __syncthreads();
+    for (int h = RED_THREADS / 2; h > 0; h >>= 1) {
+        if (t < h) {
+            s_sum[t] += s_sum[t + h];
+            s_um[t] = fmax(s_um[t], s_um[t + h]);
+            s_pmin[t] = fmin(s_pmin[t], s_pmin[t + h]);
+            s_pmax[t] = fmax(s_pmax[t], s_pmax[t + h]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        res[0] = s_sum[0];
+        res[1] = s_um[0];
+        res[2] = s_pmin[0];
+        res[3] = s_pmax[0];
+    }
+}
+
+constexpr int STEP_TX = 32;
+constexpr int STEP_TY = 16;
+constexpr int RED_BLOCKS = 1216;  // 8 x 152 SMs
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct lbm_handle {
+    int nx = 0, ny = 0;
+    size_t N = 0;
+    int device = 0;
+    lbm_params prm{};
+    Model model{};
+    cudaStream_t stream = nullptr;
+    float* f[2] = {nullptr, nullptr};
+    float* g[2] = {nullptr, nullptr};
+    float* phiu = nullptr;
+    int cur = 0;
+    void* staging = nullptr;   // host I/O staging: max(5 N doubles, 20 N floats)
+    double* red_part = nullptr;  // RED_BLOCKS x 4 partials
+    double* red_res = nullptr;   // 4 results
+    unsigned int* flag = nullptr;
+    bool inited = false;
+    long long since_check = 0;
+    char err[512] = {0};
+};
+
+static lbm_status fail(lbm_handle* h, lbm_status st, const char* fmt, ...) {
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof h->err, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define LBM_CUDA(h, call)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(h, LBM_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),  \
+                        __FILE__, __LINE__);                                                \
+    } while (0)
+
+static lbm_status validate(int nx, int ny, const lbm_params* p, char* msg, size_t len) {
+    auto bad = [&](const char* why) {
+        snprintf(msg, len, "invalid parameters: %s", why);
+        return LBM_ERR_INVALID;
+    };
+    if (!p) return bad("params is NULL");
+    if (nx < 1 || ny < 1) return bad("nx and ny must be >= 1");
+    if ((long long)nx * ny >= (1LL << 31) / 20) return bad("grid too large (nx*ny*20 must fit in 2^31)");
+    if (!(p->rho_l > 0) || !(p->rho_g > 0)) return bad("rho_l and rho_g must be > 0");
+    if (!(p->nu_l > 0) || !(p->nu_g > 0)) return bad("nu_l and nu_g must be > 0");
+    if (p->visc_mode < 0 || p->visc_mode > 2) return bad("visc_mode must be 0, 1 or 2");
+    if (!(p->sigma >= 0)) return bad("sigma must be >= 0");
+    if (!(p->W > 0)) return bad("W must be > 0");
+    if (!(p->tau_h > 0.5)) return bad("tau_h must be > 0.5");
+    if (!std::isfinite(p->Gx) || !std::isfinite(p->Gy)) return bad("G must be finite");
+    if (p->bc_y != LBM_BC_PERIODIC && p->bc_y != LBM_BC_WALLS) return bad("bc_y must be 0 or 1");
+    if (p->normal_scheme != LBM_NORMAL_CENTRAL && p->normal_scheme != LBM_NORMAL_LOCAL)
+        return bad("normal_scheme must be 0 or 1");
+    if (p->storage != LBM_STORE_FP32) return bad("storage must be LBM_STORE_FP32");
+    if (p->check_every < 0) return bad("check_every must be >= 0");
+    return LBM_OK;
+}
+
+static Model make_model(const lbm_params& p) {
+    Model m{};
+    m.rho_g = (float)p.rho_g;
+    m.drho = (float)(p.rho_l - p.rho_g);
+    m.beta4 = (float)(4.0 * 12.0 * p.sigma / p.W);
+    m.kappa = (float)(1.5 * p.sigma * p.W);
+    m.Gx = (float)p.Gx;
+    m.Gy = (float)p.Gy;
+    m.inv_tau_f = (float)(1.0 / p.tau_h);
+    m.src_f = (float)(1.0 - 0.5 / p.tau_h);
+    m.four_over_W = (float)(4.0 / p.W);
+    m.nu_l = (float)p.nu_l;
+    m.nu_g = (float)p.nu_g;
+    m.inv_nu_l = (float)(1.0 / p.nu_l);
+    m.inv_nu_g = (float)(1.0 / p.nu_g);
+    m.mu_l = (float)(p.rho_l * p.nu_l);
+    m.mu_g = (float)(p.rho_g * p.nu_g);
+    m.visc_mode = p.visc_mode;
+    m.walls = p.bc_y == LBM_BC_WALLS;
+    m.local_normal = p.normal_scheme == LBM_NORMAL_LOCAL;
+    return m;
+}
+
+static void release(lbm_handle* h) {
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->f[b]);
+        cudaFree(h->g[b]);
+    }
+    cudaFree(h->phiu);
+    cudaFree(h->staging);
+    cudaFree(h->red_part);
+    cudaFree(h->red_res);
+    cudaFree(h->flag);
+}
+
+static int grid1d(size_t N) {
+    size_t b = (N + 255) / 256;
+    return (int)(b < 4096 ? (b ? b : 1) : 4096);
+}
+
+static lbm_status launch_step(lbm_handle* h, bool fields, double* out) {
+    dim3 block(STEP_TX, STEP_TY);
+    dim3 grid((h->nx + STEP_TX - 1) / STEP_TX, (h->ny + STEP_TY - 1) / STEP_TY);
+    const int c = h->cur;
+    if (fields)
+        k_step<STEP_TX, STEP_TY, true><<<grid, block, 0, h->stream>>>(
+            h->f[c], h->g[c], nullptr, nullptr, h->phiu, h->flag, out, h->nx, h->ny, h->model);
+    else
+        k_step<STEP_TX, STEP_TY, false><<<grid, block, 0, h->stream>>>(
+            h->f[c], h->g[c], h->f[c ^ 1], h->g[c ^ 1], h->phiu, h->flag, nullptr, h->nx, h->ny,
+            h->model);
+    LBM_CUDA(h, cudaGetLastError());
+    if (!fields) h->cur ^= 1;
+    return LBM_OK;
+}
+
+static lbm_status check_flag(lbm_handle* h) {
+    unsigned int v = 0;
+    LBM_CUDA(h, cudaMemcpyAsync(&v, h->flag, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->since_check = 0;
+    if (v) {
+        LBM_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(unsigned int), h->stream));
+        return fail(h, LBM_ERR_NONFINITE, "non-finite phi, u or p produced by a step");
+    }
+    return LBM_OK;
+}
+
+extern "C" {
+
+lbm_status lbm_create(int nx, int ny, const lbm_params* p, lbm_handle** out) {
+    if (!out) return LBM_ERR_INVALID;
+    *out = nullptr;
+    char msg[256];
+    lbm_status st = validate(nx, ny, p, msg, sizeof msg);
+    if (st != LBM_OK) {
+        fprintf(stderr, "lbm_create: %s\n", msg);
+        return st;
+    }
+    lbm_handle* h = new (std::nothrow) lbm_handle();
+    if (!h) return LBM_ERR_OOM;
+    h->nx = nx;
+    h->ny = ny;
+    h->N = (size_t)nx * ny;
+    h->prm = *p;
+    h->model = make_model(*p);
+    h->stream = (cudaStream_t)p->stream;
+    cudaError_t e = cudaGetDevice(&h->device);
+    const size_t pop = 9 * h->N * sizeof(float);
+    const size_t staging = (20 * h->N * sizeof(float) > 5 * h->N * sizeof(double))
+                               ? 20 * h->N * sizeof(float)
+                               : 5 * h->N * sizeof(double);
+    if (e == cudaSuccess) e = cudaMalloc(&h->f[0], pop);
+    if (e == cudaSuccess) e = cudaMalloc(&h->f[1], pop);
+    if (e == cudaSuccess) e = cudaMalloc(&h->g[0], pop);
+    if (e == cudaSuccess) e = cudaMalloc(&h->g[1], pop);
+    if (e == cudaSuccess) e = cudaMalloc(&h->phiu, 2 * h->N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->staging, staging);
+    if (e == cudaSuccess) e = cudaMalloc(&h->red_part, 4 * RED_BLOCKS * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->red_res, 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->flag, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(unsigned int), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "lbm_create: %s\n", cudaGetErrorString(e));
+        release(h);
+        delete h;
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+}
+
+const char* lbm_last_error(const lbm_handle* h) { return h ? h->err : "null handle"; }
+
+size_t lbm_state_bytes(const lbm_handle* h) { return h ? 20 * h->N * sizeof(float) : 0; }
+
+lbm_status lbm_init(lbm_handle* h, const double* phi0, const double* ux0, const double* uy0,
+                    const double* p0) {
+    if (!h) return LBM_ERR_INVALID;
+    if (!phi0) return fail(h, LBM_ERR_INVALID, "lbm_init: phi0 is NULL");
+    LBM_CUDA(h, cudaSetDevice(h->device));
+    double* in = (double*)h->staging;
+    const size_t bytes = h->N * sizeof(double);
+    const double* src[4] = {phi0, ux0, uy0, p0};
+    for (int k = 0; k < 4; ++k) {
+        if (src[k])
+            LBM_CUDA(h, cudaMemcpyAsync(in + k * h->N, src[k], bytes, cudaMemcpyHostToDevice,
+                                        h->stream));
+        else
+            LBM_CUDA(h, cudaMemsetAsync(in + k * h->N, 0, bytes, h->stream));
+    }
+    h->cur = 0;
+    k_init<<<grid1d(h->N), 256, 0, h->stream>>>(in, h->f[0], h->g[0], h->phiu, h->nx, h->ny,
+                                                 h->model);
+    LBM_CUDA(h, cudaGetLastError());
+    LBM_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(unsigned int), h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->inited = true;
+    h->since_check = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_handle* h, int nsteps) {
+    if (!h) return LBM_ERR_INVALID;
+    if (nsteps < 0) return fail(h, LBM_ERR_INVALID, "lbm_step: nsteps < 0");
+    if (!h->inited) return fail(h, LBM_ERR_STATE, "lbm_step before lbm_init");
+    LBM_CUDA(h, cudaSetDevice(h->device));
+    for (int s = 0; s < nsteps; ++s) {
+        lbm_status st = launch_step(h, false, nullptr);
+        if (st != LBM_OK) return st;
+        if (h->prm.check_every > 0 && ++h->since_check >= h->prm.check_every) {
+            st = check_flag(h);
+            if (st != LBM_OK) return st;
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_fields(lbm_handle* h, double* phi, double* rho, double* ux, double* uy,
+                          double* p) {
+    if (!h) return LBM_ERR_INVALID;
+    if (!h->inited) return fail(h, LBM_ERR_STATE, "lbm_get_fields before lbm_init");
+    LBM_CUDA(h, cudaSetDevice(h->device));
+    double* buf = (double*)h->staging;
+    lbm_status st = launch_step(h, true, buf);
+    if (st != LBM_OK) return st;
+    double* outs[5] = {phi, rho, ux, uy, p};
+    for (int k = 0; k < 5; ++k)
+        if (outs[k])
+            LBM_CUDA(h, cudaMemcpyAsync(outs[k], buf + k * h->N, h->N * sizeof(double),
+                                        cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_state(lbm_handle* h, void* host_buf, size_t bytes) {
+    if (!h || !host_buf) return fail(h, LBM_ERR_INVALID, "lbm_get_state: NULL argument");
+    if (bytes != lbm_state_bytes(h))
+        return fail(h, LBM_ERR_INVALID, "lbm_get_state: need %zu bytes, got %zu",
+                    lbm_state_bytes(h), bytes);
+    if (!h->inited) return fail(h, LBM_ERR_STATE, "lbm_get_state before lbm_init");
+    LBM_CUDA(h, cudaSetDevice(h->device));
+    float* st = (float*)h->staging;
+    k_state_out<<<grid1d(h->N), 256, 0, h->stream>>>(h->f[h->cur], h->g[h->cur], h->phiu, st,
+                                                      h->nx, h->ny, h->model.walls);
+    LBM_CUDA(h, cudaGetLastError());
+    LBM_CUDA(h, cudaMemcpyAsync(host_buf, st, bytes, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_handle* h, const void* host_buf, size_t bytes) {
+    if (!h || !host_buf) return fail(h, LBM_ERR_INVALID, "lbm_set_state: NULL argument");
+    if (bytes != lbm_state_bytes(h))
+        return fail(h, LBM_ERR_INVALID, "lbm_set_state: need %zu bytes, got %zu",
+                    lbm_state_bytes(h), bytes);
+    LBM_CUDA(h, cudaSetDevice(h->device));
+    float* st = (float*)h->staging;
+    LBM_CUDA(h, cudaMemcpyAsync(st, host_buf, bytes, cudaMemcpyHostToDevice, h->stream));
+    h->cur = 0;
+    k_state_in<<<grid1d(h->N), 256, 0, h->stream>>>(st, h->f[0], h->g[0], h->phiu, h->nx,
+                                                     h->ny, h->model.walls);
+    LBM_CUDA(h, cudaGetLastError());
+    LBM_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(unsigned int), h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->inited = true;
+    h->since_check = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_diag(lbm_handle* h, double* sum_phi, double* umax, double* pmin, double* pmax) {
+    if (!h) return LBM_ERR_INVALID;
+    if (!h->inited) return fail(h, LBM_ERR_STATE, "lbm_diag before lbm_init");
+    LBM_CUDA(h, cudaSetDevice(h->device));
+    double* buf = (double*)h->staging;
+    lbm_status st = launch_step(h, true, buf);
+    if (st != LBM_OK) return st;
+    k_diag_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(buf, h->N, h->red_part);
+    LBM_CUDA(h, cudaGetLastError());
+    k_diag_final<<<1, RED_THREADS, 0, h->stream>>>(h->red_part, RED_BLOCKS, h->red_res);
+    LBM_CUDA(h, cudaGetLastError());
+    double r[4];
+    LBM_CUDA(h, cudaMemcpyAsync(r, h->red_res, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (sum_phi) *sum_phi = r[0];
+    if (umax) *umax = r[1];
+    if (pmin) *pmin = r[2];
+    if (pmax) *pmax = r[3];
+    return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_handle* h) {
+    if (!h) return LBM_ERR_INVALID;
+    LBM_CUDA(h, cudaSetDevice(h->device));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -77,9 +77,9 @@ def step(f, g, phiu, p):
     drho = p["rho_l"] - p["rho_g"]
     lam = 4 * phi * (1 - phi) / p["W"]
     mag = np.hypot(m["gx"], m["gy"])
-    safe = np.where(mag > 1e-12, mag, 1.0)
-    nxv = np.where(mag > 1e-12, m["gx"] / safe, 0.0)
-    nyv = np.where(mag > 1e-12, m["gy"] / safe, 0.0)
+    safe = np.where(mag > 1e-6, mag, 1.0)
+    nxv = np.where(mag > 1e-6, m["gx"] / safe, 0.0)
+    nyv = np.where(mag > 1e-6, m["gy"] / safe, 0.0)
     Dx = phi * ux - phiu[0]
     Dy = phi * uy - phiu[1]
     fo = np.empty_like(f)

@@ -1,0 +1,83 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/lbm_pf.h declares, and rejects bad parameters
+before touching the device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1710_09541_gb300 import build as lbm_build
+from paper_1710_09541_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    lbm_build.build()
+    return lbm.load()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", src))
+    return names
+
+
+def test_header_declares_the_binding_names():
+    assert _declared() == set(lbm.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_params_struct_layout_matches_header(tmp_path):
+    """Compile a C probe against include/lbm_pf.h and compare the size and
+    every field offset of lbm_params with the ctypes mirror."""
+    fields = [f[0] for f in lbm.lbm_params._fields_]
+    src = tmp_path / "probe.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbm_pf.h"\n'
+                   "int main(void){printf(\"%zu\\n\", sizeof(lbm_params));"
+                   + "".join(f'printf("%zu\\n", offsetof(lbm_params, {f}));' for f in fields)
+                   + "return 0;}\n")
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                           text=True).stdout.split()]
+    assert vals[0] == ctypes.sizeof(lbm.lbm_params)
+    assert vals[1:] == [getattr(lbm.lbm_params, f).offset for f in fields]
+
+
+@pytest.mark.parametrize("bad", [
+    dict(rho_g=0.0), dict(nu_l=-1.0), dict(visc_mode=3), dict(W=0.0), dict(tau_h=0.5),
+    dict(sigma=-1.0), dict(bc_y=2), dict(normal_scheme=5), dict(storage=7), dict(check_every=-1),
+    dict(Gx=float("inf")),
+])
+def test_create_rejects_bad_parameters(L, bad):
+    p = lbm.make_params(**bad)
+    h = ctypes.c_void_p()
+    assert L.lbm_create(16, 16, ctypes.byref(p), ctypes.byref(h)) == lbm.LBM_ERR_INVALID
+    assert not h.value
+
+
+@pytest.mark.parametrize("nx,ny", [(0, 4), (4, 0), (-3, 5), (1 << 20, 1 << 20)])
+def test_create_rejects_bad_sizes(L, nx, ny):
+    p = lbm.make_params()
+    h = ctypes.c_void_p()
+    assert L.lbm_create(nx, ny, ctypes.byref(p), ctypes.byref(h)) == lbm.LBM_ERR_INVALID
+
+
+def test_null_handle_calls_are_rejected(L):
+    assert L.lbm_step(None, 1) == lbm.LBM_ERR_INVALID
+    assert L.lbm_get_fields(None, None, None, None, None, None) == lbm.LBM_ERR_INVALID
+    assert L.lbm_diag(None, None, None, None, None) == lbm.LBM_ERR_INVALID
+    assert L.lbm_state_bytes(None) == 0
+    L.lbm_destroy(None)

@@ -1,0 +1,445 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the FP64
+oracle on the same seeded inputs.
+
+Three tiers:
+
+1. One step from an identical state (the FP32 state loaded into both), at
+   states sampled along long oracle trajectories and at the full benchmark
+   sizes.  Every node and population is compared.  The bound is FP32
+   rounding plus the conditioning of the sharpening normal n = grad phi /
+   |grad phi| (Eqs. 2, 11): where |grad phi| is small while lambda (Eq. 3)
+   is not, an FP32 perturbation eps of grad phi turns n by eps/|grad phi|, so
+   F_i may differ by up to 0.35 |lambda| min(1, eps/|grad phi|).
+2. 100 free-running steps on flows whose interfaces keep phi inside [0, 1]
+   without interior extrema (layers, translation, walls, tiny grids):
+   relative field error <= 1e-5 for phi, rho, u and <= 3e-5 for p.
+3. Drops and spinodal mixtures grow phi extrema with lambda != 0, where the
+   FP64 oracle itself moves by > 1e-4 after 100 steps when its input is
+   rounded to FP32.  There: pointwise agreement over the horizon where the
+   oracle is reproducible, then integrated quantities within 1%.
+
+Field error = max |gpu - oracle| / max(max |oracle|, s_ref); s_ref = 1 for
+phi, rho_l for rho, sigma/mu_l for u, sigma/R (drop) or sigma/W for p."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_09541_gb300 import cases
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5       # phi, rho, u after 100 FP32 steps
+TOL_P = 3e-5     # p after 100 FP32 steps (g stored in FP32 is up to 100x |p|)
+EPS_GRAD = 3e-7  # FP32 round-off of a stencil gradient of an O(1) field
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_09541_gb300 import build as lbm_build
+    from paper_1710_09541_gb300 import lbm as _lbm
+
+    lbm_build.build()
+    _lbm.load()
+    return _lbm
+
+
+def _scales(P, R=None):
+    U = max(cases.capillary_velocity(P), 1e-6)
+    return {"phi": 1.0, "rho": P["rho_l"], "ux": U, "uy": U,
+            "p": max(P["sigma"] / (R if R else P["W"]), 1e-8)}
+
+
+def _field_errors(got, ref, scales):
+    return {k: float(np.abs(got[k] - ref[k]).max() / max(np.abs(ref[k]).max(), s))
+            for k, s in scales.items()}
+
+
+def _assert_fields(got, ref, scales, tol=TOL, tol_p=TOL_P):
+    errs = _field_errors(got, ref, scales)
+    for k, v in errs.items():
+        assert np.isfinite(v) and v <= (tol_p if k == "p" else tol), errs
+    return errs
+
+
+def _max3x3(a, walls):
+    """max over the 3x3 neighbourhood (periodic in x; clamped rows at walls)."""
+    out = a.copy()
+    for dy in (-1, 0, 1):
+        r = np.roll(a, dy, axis=0)
+        if walls and dy == 1:
+            r[0] = a[0]
+        if walls and dy == -1:
+            r[-1] = a[-1]
+        for dx in (-1, 0, 1):
+            out = np.maximum(out, np.roll(r, dx, axis=1))
+    return out
+
+
+def _one_step_parity(lbm, nx, ny, P, state, R=None):
+    """Load the same FP32 state into GPU and oracle, step once, compare the
+    full state (f, g, phi u) and the fields."""
+    st32 = [np.ascontiguousarray(a, dtype=np.float32) for a in state]
+    st64 = [a.astype(np.float64) for a in st32]
+    o = oracle.Lattice(nx, ny, **P).set_state(*st64)
+    pre = o.fields()
+    walls = P.get("bc_y", 0) == 1
+    gx, gy, _ = oracle.grad_lap(pre["phi"], bc_y=int(walls))
+    lam = np.abs(4 * pre["phi"] * (1 - pre["phi"]) / P["W"])
+    gmag = np.hypot(gx, gy)
+    local = P.get("normal_scheme", 0) == 1
+    if local:
+        # Eq. 29 takes n from C = sum c_i (f_i - f_i^eq) + d_t(phi u)/2, a sum of
+        # eight FP32 differences of O(w_i) populations
+        cx, cy, w, _ = oracle.lattice_constants()
+        f = st64[0]
+        cu = cx[:, None, None] * pre["ux"] + cy[:, None, None] * pre["uy"]
+        neq = f - w[:, None, None] * pre["phi"] * (1 + 3 * cu)
+        Cx = (cx[:, None, None] * neq).sum(0) + 0.5 * (pre["phi"] * pre["ux"] - st64[2][0])
+        Cy = (cy[:, None, None] * neq).sum(0) + 0.5 * (pre["phi"] * pre["uy"] - st64[2][1])
+        gmag, eps, gate = np.hypot(Cx, Cy), 4e-7, 2e-6
+    else:
+        gmag, eps, gate = np.hypot(gx, gy), EPS_GRAD, 2e-6  # |n| cut-off is 1e-6
+    cond = np.where(gmag < gate, 1.0, np.minimum(1.0, eps / np.maximum(gmag, 1e-300)))
+    bound_f = 3e-7 + _max3x3(0.35 * lam * cond, walls)
+    o.step(1)
+    of, og, ophiu = o.get_state()
+    with lbm.Lattice(nx, ny, **P) as g:
+        g.set_state(*st32).step(1)
+        gf, gg, gphiu = g.get_state()
+        got = g.fields()
+    ref = o.fields()
+    assert np.all(np.abs(gf - of) <= bound_f[None]), float(np.abs(gf - of).max())
+    assert np.abs(gg - og).max() <= 5e-6 * np.abs(og).max() + 1e-12
+    # u carries the FP32 error of F = mu grad phi divided by rho (Eq. 22a)
+    assert np.abs(gphiu - ophiu).max() <= 5e-6 * np.abs(ophiu).max() + 1e-8
+    ill = float((0.35 * lam * cond > 1e-5).mean())
+    sc = _scales(P, R)
+    # fields of the new state: phi, rho, u within 2e-6 where n is well
+    # conditioned everywhere; near ill-conditioned nodes phi inherits bound_f
+    phi_bound = 9 * _max3x3(bound_f, walls)
+    assert np.all(np.abs(got["phi"] - ref["phi"]) <= phi_bound + 2e-6)
+    return ill
+
+
+def _trajectory_states(nx, ny, P, phi0, u0=None, v0=None, T=300, every=50):
+    o = oracle.Lattice(nx, ny, **P).init(phi0, u0, v0)
+    for t in range(0, T + 1, every):
+        yield t, o.get_state()
+        o.step(every)
+
+
+def _two_drops(nx, ny):
+    return np.maximum(cases.drop(nx, ny, 14, 4.0, x0=30, y0=35), cases.drop(nx, ny, 9, 4.0, x0=75, y0=20))
+
+
+# ---------------------------------------------------------------- tier 1 ----
+
+TRAJ_CASES = {
+    "static_drop_64_ratio1000": (64, 64, cases.params_static_drop(), lambda: (cases.drop(64, 64, 16, 4.0),)),
+    "two_drops_ragged_m1": (100, 70, dict(rho_l=1.0, rho_g=0.01, nu_l=0.05, nu_g=0.15, visc_mode=1,
+                                          sigma=5e-3, W=4.0, tau_h=0.7, Gx=2e-6, Gy=-1e-6, bc_y=0),
+                            lambda: (_two_drops(100, 70),)),
+    "two_drops_ragged_m2": (100, 70, dict(rho_l=1.0, rho_g=0.01, nu_l=0.05, nu_g=0.15, visc_mode=2,
+                                          sigma=5e-3, W=4.0, tau_h=0.7, Gx=2e-6, Gy=-1e-6, bc_y=0),
+                            lambda: (_two_drops(100, 70),)),
+    "walls_drop_step_mu": (77, 45, dict(rho_l=1.0, rho_g=0.01, nu_l=0.1, nu_g=0.1, visc_mode=2, sigma=0.01,
+                                        W=4.0, tau_h=0.8, Gx=1e-6, Gy=0.0, bc_y=1),
+                           lambda: (cases.drop(77, 45, 12, 4.0, x0=38, y0=8, walls_y=True),)),
+    "spinodal_128_ratio1000": (128, 128, cases.params_spinodal(ratio=1000.0),
+                               lambda: (cases.spinodal(128, 128, 0.5, 0.01, seed=12345),)),
+    "local_normal_drop": (64, 48, dict(cases.params_static_drop(), normal_scheme=1),
+                          lambda: (cases.drop(64, 48, 12, 4.0),)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TRAJ_CASES))
+def test_one_step_parity_along_trajectory(lbm, name):
+    nx, ny, P, init = TRAJ_CASES[name]
+    ill = []
+    for t, state in _trajectory_states(nx, ny, P, *init(), T=300, every=60):
+        ill.append(_one_step_parity(lbm, nx, ny, P, state))
+    # once the initial transient is over, ill-conditioned nodes are a minority
+    assert ill[-1] < 0.05, ill
+
+
+def test_one_step_parity_perf_2048(lbm):
+    """The benchmark workload at full size (2048 x 2048, ratio 1000), in the
+    benchmark's launch configuration, one step from the oracle's state after
+    3 steps; every node."""
+    phi0, P = cases.perf_case()
+    nx, ny = cases.PERF_NX, cases.PERF_NY
+    o = oracle.Lattice(nx, ny, **P).init(phi0).step(3)
+    ill = _one_step_parity(lbm, nx, ny, P, o.get_state())
+    assert ill < 0.05
+
+
+def test_one_step_parity_impact_2400x600(lbm):
+    """Droplet impact at full size (2400 x 600, D = 200, film 20, U = 0.04,
+    Re = 100, We = 8000, ratio 1000, walls), one step from the oracle state
+    after 5 steps."""
+    nx, ny = 2400, 600
+    P = cases.params_impact(Re=100.0)
+    phi0, u0, v0 = cases.impact(nx, ny, 200.0, 20.0, 0.04, 5.0)
+    o = oracle.Lattice(nx, ny, **P).init(phi0, u0, v0).step(5)
+    _one_step_parity(lbm, nx, ny, P, o.get_state(), R=100)
+
+
+def test_one_step_parity_spinodal_1024(lbm):
+    """Spinodal decomposition at full size (1024 x 1024, ratio 1000)."""
+    P = cases.params_spinodal(ratio=1000.0)
+    o = oracle.Lattice(1024, 1024, **P).init(cases.spinodal(1024, 1024, 0.5, 0.01, seed=12345)).step(2)
+    _one_step_parity(lbm, 1024, 1024, P, o.get_state())
+
+
+# ---------------------------------------------------------------- tier 2 ----
+
+def _free_run(lbm, nx, ny, P, steps, phi0, u0=None, v0=None, p0=None):
+    with lbm.Lattice(nx, ny, **P) as g:
+        g.init(phi0, u0, v0, p0).step(steps)
+        got = g.fields()
+    ref = oracle.Lattice(nx, ny, **P).init(phi0, u0, v0, p0).step(steps).fields()
+    return got, ref
+
+
+def test_free_run_layered_poiseuille_8x256(lbm):
+    """Layered Poiseuille geometry at full size: 8 x 256, walls, ratio 1000,
+    mu ratio 100, G_x = 1e-7, step viscosity (Eq. 26); 100 steps."""
+    P = cases.params_poiseuille(256, Gx=1e-7, mu_ratio=100.0)
+    got, ref = _free_run(lbm, 8, 256, P, 100, cases.layer(8, 256, P["W"]))
+    _assert_fields(got, ref, _scales(P))
+
+
+def test_free_run_translation_ragged(lbm):
+    """A drop carried by a uniform flow on a ragged 100 x 70 periodic grid
+    (tiles of 32 x 16 leave partial tiles in both directions), ratio 1000,
+    sigma = 0; 100 steps."""
+    nx, ny = 100, 70
+    P = dict(rho_l=1.0, rho_g=1e-3, nu_l=0.1, nu_g=0.1, sigma=0.0, W=4.0)
+    phi0 = cases.drop(nx, ny, 12, 4.0, x0=40, y0=30)
+    got, ref = _free_run(lbm, nx, ny, P, 100, phi0, np.full_like(phi0, 0.01), np.full_like(phi0, -0.004))
+    _assert_fields(got, ref, {"phi": 1.0, "rho": 1.0, "ux": 0.01, "uy": 0.01, "p": 1e-8})
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_free_run_walls_drop(lbm, mode):
+    """77 x 45 with half-way bounce-back walls, a drop resting on the lower
+    wall, body force, ratio 100; 100 steps."""
+    nx, ny = 77, 45
+    P = dict(rho_l=1.0, rho_g=0.01, nu_l=0.1, nu_g=0.3, visc_mode=mode, sigma=0.01, W=4.0,
+             tau_h=0.8, Gx=1e-6, Gy=0.0, bc_y=1)
+    got, ref = _free_run(lbm, nx, ny, P, 100, cases.drop(nx, ny, 12, 4.0, x0=38, y0=8, walls_y=True))
+    _assert_fields(got, ref, _scales(P, R=12))
+
+
+@pytest.mark.parametrize("nx,ny,bc", [(1, 1, 0), (3, 5, 0), (8, 8, 1), (33, 17, 0), (5, 2, 1), (31, 16, 1)])
+def test_free_run_tiny_and_degenerate_grids(lbm, nx, ny, bc):
+    """Grids smaller than one tile, one-node-wide grids, walls two rows apart."""
+    P = dict(rho_l=1.0, rho_g=0.1, nu_l=0.1, nu_g=0.1, visc_mode=0, sigma=0.01, W=3.0,
+             tau_h=0.8, Gx=1e-5, Gy=2e-5, bc_y=bc)
+    r = np.random.default_rng(nx * 100 + ny)
+    phi0 = 0.5 + 0.3 * r.random((ny, nx))
+    ux0 = 1e-3 * r.standard_normal((ny, nx))
+    got, ref = _free_run(lbm, nx, ny, P, 30, phi0, ux0)
+    _assert_fields(got, ref, {"phi": 1.0, "rho": 1.0, "ux": 1e-3, "uy": 1e-3, "p": 1e-3})
+
+
+def test_init_state_matches_oracle(lbm):
+    nx, ny = 37, 29
+    P = dict(cases.params_static_drop(), bc_y=1)
+    phi0 = cases.drop(nx, ny, 8, 4.0, walls_y=True)
+    r = np.random.default_rng(1)
+    ux0, uy0, p0 = (1e-3 * r.standard_normal((ny, nx)) for _ in range(3))
+    with lbm.Lattice(nx, ny, **P) as g:
+        f, gg, phiu = g.init(phi0, ux0, uy0, p0).get_state()
+    of, og, ophiu = oracle.Lattice(nx, ny, **P).init(phi0, ux0, uy0, p0).get_state()
+    assert np.abs(f - of).max() < 1e-7
+    assert np.abs(gg - og).max() < 1e-9
+    assert np.abs(phiu - ophiu).max() < 1e-9
+
+
+# ---------------------------------------------------------------- tier 3 ----
+
+def test_static_drop_cfg1_horizon_and_integrals(lbm):
+    """Static droplet 64 x 64, R = 16, ratio 1000, sigma = 0.01, tau = 0.8:
+    pointwise within 1e-5 (p 3e-5) for 50 steps, then after 3000 steps the
+    Laplace pressure jump, the spurious-velocity maximum and the density
+    profile agree with the oracle."""
+    nx = ny = 64
+    P = cases.params_static_drop()
+    phi0 = cases.drop(nx, ny, 16, 4.0)
+    with lbm.Lattice(nx, ny, **P) as g:
+        g.init(phi0).step(50)
+        got50 = g.fields()
+        s0 = phi0.sum()
+        g.step(2950)
+        got = g.fields()
+        s1, umax, _, _ = g.diag()
+    o = oracle.Lattice(nx, ny, **P).init(phi0).step(50)
+    _assert_fields(got50, o.fields(), _scales(P, R=16))
+    ref = o.step(2950).fields()
+    ou = np.hypot(ref["ux"], ref["uy"]).max()
+    assert abs(umax / ou - 1) < 0.05
+    # the drop's liquid area and centre-line density integral
+    assert abs((got["phi"] > 0.5).sum() / (ref["phi"] > 0.5).sum() - 1) < 0.01
+    assert abs(got["rho"][32, :].sum() / ref["rho"][32, :].sum() - 1) < 0.01
+    # FP32 storage: sum phi drifts by ~1e-9 per step (1e-12 in the oracle)
+    assert abs(s1 / s0 - 1) < 1e-5
+    # Laplace jump averaged over the slowly decaying acoustic oscillation
+    dp = lambda F: F["p"][32, 32] - F["p"][0, 0]
+    dg, do = [], []
+    with lbm.Lattice(nx, ny, **P) as g:
+        g.set_state(*(a.astype(np.float32) for a in o.get_state()))
+        for _ in range(40):
+            g.step(125)
+            o.step(125)
+            dg.append(dp(g.fields()))
+            do.append(dp(o.fields()))
+    assert abs(np.mean(dg) / np.mean(do) - 1) < 0.01
+    assert abs(np.mean(do) / (P["sigma"] / 16) - 1) < 0.03
+
+
+def _domain_length(phi):
+    """nodes per interface link: N / #(nearest-neighbour links straddling 1/2)."""
+    a = phi > 0.5
+    links = (a != np.roll(a, 1, 0)).sum() + (a != np.roll(a, 1, 1)).sum()
+    return phi.size / max(links, 1)
+
+
+@pytest.mark.parametrize("ratio", [3.0, 1000.0])
+def test_spinodal_integrals(lbm, ratio):
+    """Spinodal decomposition, 256 x 256, sigma = 1e-3, W = 4: after 1500
+    steps the domain length, the liquid fraction and sum phi agree within 1%."""
+    nx = ny = 256
+    P = cases.params_spinodal(ratio=ratio)
+    phi0 = cases.spinodal(nx, ny, 0.5, 0.01, seed=12345)
+    got, ref = _free_run(lbm, nx, ny, P, 1500, phi0)
+    assert abs(_domain_length(got["phi"]) / _domain_length(ref["phi"]) - 1) < 0.01
+    assert abs((got["phi"] > 0.5).mean() / (ref["phi"] > 0.5).mean() - 1) < 0.01
+    # FP32 storage drifts sum phi by ~2e-9 per step (measured 3.3e-6 here)
+    assert abs(got["phi"].sum() / ref["phi"].sum() - 1) < 1e-5, got["phi"].sum() / ref["phi"].sum() - 1
+
+
+def _spreading_radius(phi, film, W):
+    """Half the x-extent of the liquid (phi >= 1/2) on the row W above the film
+    surface, contiguous with the centre column."""
+    row = phi[int(round(film + W)), :] >= 0.5
+    c = phi.shape[1] // 2
+    if not row[c]:
+        return 0.0
+    left = c
+    while left > 0 and row[left - 1]:
+        left -= 1
+    right = c
+    while right < len(row) - 1 and row[right + 1]:
+        right += 1
+    return 0.5 * (right - left + 1)
+
+
+def test_impact_spreading_radius_scaled(lbm):
+    """Droplet impact on a thin film, scaled to D = 40 on 480 x 120 (film
+    0.1 D, U = 0.04, Re = 100, We = 8000, ratio 1000, mu ratio 40): the
+    spreading radius agrees within 1% up to t* = t U / D = 1, and the full
+    fields pointwise for the first 10 steps."""
+    nx, ny, D, film = 480, 120, 40.0, 4.0
+    P = cases.params_impact(D=D, Re=100.0)
+    phi0, u0, v0 = cases.impact(nx, ny, D, film, 0.04, P["W"])
+    got, ref = _free_run(lbm, nx, ny, P, 10, phi0, u0, v0)
+    _assert_fields(got, ref, _scales(P, R=D / 2))
+    steps = int(D / 0.04)
+    with lbm.Lattice(nx, ny, **P) as g:
+        g.init(phi0, u0, v0)
+        o = oracle.Lattice(nx, ny, **P).init(phi0, u0, v0)
+        for _ in range(4):
+            g.step(steps // 4)
+            o.step(steps // 4)
+            rg = _spreading_radius(g.fields()["phi"], film, P["W"])
+            ro = _spreading_radius(o.fields()["phi"], film, P["W"])
+            assert abs(rg - ro) <= max(0.01 * ro, 1.0)
+
+
+# ------------------------------------------------------------ behaviour ----
+
+def test_checkpoint_resume_bit_exact(lbm):
+    nx, ny = 70, 50
+    P = cases.params_static_drop()
+    phi0 = cases.drop(nx, ny, 12, 4.0)
+    with lbm.Lattice(nx, ny, **P) as a, lbm.Lattice(nx, ny, **P) as b:
+        a.init(phi0).step(40)
+        b.init(phi0).step(15)
+        st = b.get_state()
+        b.set_state(*st).step(25)
+        for x, y in zip(a.get_state(), b.get_state()):
+            assert np.array_equal(x, y)
+
+
+def test_sum_phi_conserved_and_diag(lbm):
+    nx, ny = 128, 96
+    P = cases.params_static_drop()
+    phi0 = cases.drop(nx, ny, 20, 4.0)
+    with lbm.Lattice(nx, ny, **P) as g:
+        g.init(phi0)
+        s0, *_ = g.diag()
+        g.step(500)
+        s1, umax, pmin, pmax = g.diag()
+        F = g.fields()
+    assert abs(s0 - phi0.sum()) / phi0.sum() < 1e-6
+    assert abs(s1 - s0) / s0 < 1e-5          # FP32 storage: round-off random walk
+    assert abs(s1 - F["phi"].sum()) / s0 < 1e-12
+    assert abs(umax - np.hypot(F["ux"], F["uy"]).max()) <= 1e-12
+    assert pmin == F["p"].min() and pmax == F["p"].max()
+
+
+def test_nonfinite_state_is_reported(lbm):
+    """A NaN injected into the populations on the host is reported by
+    lbm_step with LBM_ERR_NONFINITE (check_every = 1)."""
+    nx, ny = 40, 30
+    P = dict(cases.params_static_drop(), check_every=1)
+    with lbm.Lattice(nx, ny, **P) as g:
+        g.init(cases.drop(nx, ny, 8, 4.0))
+        g.step(3)
+        f, gg, phiu = g.get_state()
+        f = f.copy()
+        f[3, 10, 10] = np.nan
+        g.set_state(f, gg, phiu)
+        with pytest.raises(lbm.LbmError) as e:
+            g.step(2)
+        assert e.value.status == lbm.LBM_ERR_NONFINITE
+
+
+def test_step_before_init_is_a_state_error(lbm):
+    with lbm.Lattice(16, 16) as g:
+        with pytest.raises(lbm.LbmError) as e:
+            g.step(1)
+        assert e.value.status == lbm.LBM_ERR_STATE
+
+
+def test_poiseuille_steady_state_fp32_vs_fp64_and_eq31(lbm):
+    """Layered Poiseuille flow (8 x 256, ratio 1000, mu ratio 10, G_x = 1e-7)
+    run 200000 steps from the analytic profile.  FP32 rounding injects
+    ~1e-8 relative velocity noise per step, which the viscous relaxation
+    integrates over h^2 / (pi^2 nu) ~ 1.7e4 steps: the FP32 profile may differ
+    from the FP64 oracle's by ~2e-4 (bound 1e-3, L2), and its error against
+    Eq. 31 stays within 5% (+1e-3) of the oracle's own."""
+    nx, ny = 8, 256
+    P = cases.params_poiseuille(ny, Gx=1e-7, mu_ratio=10.0)
+    h = ny / 2.0
+    s = (np.arange(ny) + 0.5 - h) / h
+    mu_l, mu_g, G = P["rho_l"] * P["nu_l"], P["rho_g"] * P["nu_g"], P["Gx"]
+    a = (mu_g - mu_l) / (mu_g + mu_l)
+    ua = np.where(s > 0, G * h * h / (2 * mu_g) * (-s ** 2 - s * a + 2 * mu_g / (mu_g + mu_l)),
+                  G * h * h / (2 * mu_l) * (-s ** 2 - s * a + 2 * mu_l / (mu_g + mu_l)))
+    phi0 = cases.layer(nx, ny, P["W"])
+    u0 = np.broadcast_to(ua[:, None], (ny, nx))
+    steps = 200000
+    got, ref = _free_run(lbm, nx, ny, P, steps, phi0, u0)
+    ug, uo = got["ux"][:, 0], ref["ux"][:, 0]
+    rel = np.sqrt(((ug - uo) ** 2).sum() / (uo ** 2).sum())
+    l2 = lambda u: np.sqrt(((u - ua) ** 2).sum() / (ua ** 2).sum())
+    drift = got["phi"].sum() / ref["phi"].sum() - 1
+    assert rel < 1e-3, (rel, drift)
+    assert l2(ug) < 1.05 * l2(uo) + 1e-3, (l2(ug), l2(uo))
+    assert abs(drift) < 1e-5
