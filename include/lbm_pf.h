@@ -139,6 +139,37 @@ lbm_status lbm_set_state(lbm_handle* h, const void* host_buf, size_t bytes);
 lbm_status lbm_diag(lbm_handle* h, double* sum_phi, double* umax, double* pmin,
                     double* pmax);
 
+/*
+ * lbm_diag_fields_noalloc -- the reductions of lbm_diag (sum of phi in FP64,
+ * max |u|, min p, max p) over fields the caller already holds on the device,
+ * without allocating anything.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory at this point, such
+ * as a process whose device memory belongs to its own pool or runtime (a
+ * cudaMalloc behind its back breaks its accounting or fails), or a stepping
+ * loop that must not synchronise the device (cudaMalloc/cudaFree can).
+ *   d_fields  device array of 5*n doubles: planes phi, rho, ux, uy, p of n
+ *             nodes each (the layout lbm_get_fields fills; rho is not read).
+ *   n         node count, 0 <= n <= 16,777,216 (4096^2); larger n returns
+ *             LBM_ERR_INVALID and explains the limit in err.
+ *   d_out     device array of 4 doubles receiving sum phi, max |u|, min p,
+ *             max p (for n = 0: 0, 0, +inf, -inf).
+ *   stream    cudaStream_t to enqueue on (NULL = default stream); the call
+ *             returns after enqueueing, d_out is ready when the stream is.
+ *   err, err_len  optional host buffer for a one-line error message.
+ * The block partials live in a fixed 128 KiB array inside the library image,
+ * which every GPU that loads the library holds until the process exits.  The
+ * first call on each device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  All calls
+ * on a device share the array: calls whose kernels overlap on the GPU (on
+ * different streams, or from different threads) race and must be ordered by
+ * the caller.  The array keeps the previous call's partials; each call
+ * rewrites every slot it reads, so nothing needs clearing.  Errors:
+ * LBM_ERR_INVALID (NULL pointer, n too large), LBM_ERR_CUDA (no device,
+ * symbol lookup or launch failure).
+ */
+lbm_status lbm_diag_fields_noalloc(const double* d_fields, size_t n, double* d_out, void* stream,
+                                   char* err, size_t err_len);
+
 /* lbm_synchronize -- wait for all work enqueued by this handle. */
 lbm_status lbm_synchronize(lbm_handle* h);
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "lbm_kernels.cuh"
@@ -598,3 +599,93 @@ lbm_status lbm_synchronize(lbm_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free grid reduction.
+//
+// Some callers may not allocate device memory at the point where they want
+// diagnostics: a host process whose device memory is handed out by its own
+// pool or runtime (so a cudaMalloc behind its back would break its
+// accounting or fail outright), or a time-stepping loop that must not
+// synchronise the device, which cudaMalloc and cudaFree can do.
+// lbm_diag_fields_noalloc serves them: it reduces fields the caller already
+// holds on the device, with the block partials in the file-scope array below
+// instead of the handle's cudaMalloc'd buffer.  The array is part of the
+// library image, so every GPU that loads the library holds it (128 KiB) until
+// the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int NOALLOC_MAX_BLOCKS = 4096;       // partials the array can hold
+constexpr size_t NOALLOC_PER_BLOCK = 4096;     // elements reduced per block
+constexpr size_t NOALLOC_MAX_N = NOALLOC_MAX_BLOCKS * NOALLOC_PER_BLOCK;  // 16,777,216
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) double g_noalloc_part[4 * NOALLOC_MAX_BLOCKS];
+
+// Host-side: the array's name is only a host stand-in, never a device
+// address.  Its device address is looked up once per device (with that device
+// current) and cached here.
+static std::atomic<void*> g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+static void noalloc_msg(char* err, size_t len, const char* fmt, ...) {
+    if (!err || len == 0) return;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(err, len, fmt, ap);
+    va_end(ap);
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_diag_fields_noalloc(const double* d_fields, size_t n, double* d_out,
+                                              void* stream, char* err, size_t err_len) {
+    if (err && err_len) err[0] = '\0';
+    if (!d_fields && n > 0) {
+        noalloc_msg(err, err_len, "lbm_diag_fields_noalloc: d_fields is NULL");
+        return LBM_ERR_INVALID;
+    }
+    if (!d_out) {
+        noalloc_msg(err, err_len, "lbm_diag_fields_noalloc: d_out is NULL");
+        return LBM_ERR_INVALID;
+    }
+    if (n > NOALLOC_MAX_N) {
+        noalloc_msg(err, err_len,
+                    "lbm_diag_fields_noalloc: n = %zu exceeds the maximum of %zu nodes "
+                    "(%d static partial slots x %zu nodes each)",
+                    n, NOALLOC_MAX_N, NOALLOC_MAX_BLOCKS, NOALLOC_PER_BLOCK);
+        return LBM_ERR_INVALID;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        noalloc_msg(err, err_len, "lbm_diag_fields_noalloc: no usable current device (%s)",
+                    cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    // set-up on the first call on this device: find the array's device address
+    double* part = (double*)g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!part) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_part);
+        if (e != cudaSuccess || !ptr) {
+            noalloc_msg(err, err_len, "lbm_diag_fields_noalloc: cudaGetSymbolAddress failed: %s",
+                        cudaGetErrorString(e));
+            return LBM_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev].store(ptr, std::memory_order_release);
+        part = (double*)ptr;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // every slot the final pass reads is rewritten by this call's first pass
+    const int nb = (int)((n + NOALLOC_PER_BLOCK - 1) / NOALLOC_PER_BLOCK);
+    if (nb > 0) k_diag_partial<<<nb, RED_THREADS, 0, s>>>(d_fields, n, part);
+    k_diag_final<<<1, RED_THREADS, 0, s>>>(part, nb, d_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        noalloc_msg(err, err_len, "lbm_diag_fields_noalloc: launch failed: %s",
+                    cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}

@@ -30,7 +30,7 @@ LBM_STORE_FP32 = 0
 # every entry point include/lbm_pf.h declares
 EXPORTS = ("lbm_create", "lbm_init", "lbm_step", "lbm_get_fields", "lbm_state_bytes",
            "lbm_get_state", "lbm_set_state", "lbm_diag", "lbm_synchronize", "lbm_destroy",
-           "lbm_last_error")
+           "lbm_last_error", "lbm_diag_fields_noalloc")
 
 
 class LbmError(RuntimeError):
@@ -80,6 +80,8 @@ def load() -> ctypes.CDLL:
     L.lbm_destroy.restype = None
     L.lbm_last_error.argtypes = [vp]
     L.lbm_last_error.restype = ctypes.c_char_p
+    L.lbm_diag_fields_noalloc.argtypes = [vp, sz, vp, vp, ctypes.c_char_p, sz]
+    L.lbm_diag_fields_noalloc.restype = ctypes.c_int
     for name in ("lbm_create", "lbm_init", "lbm_step", "lbm_get_fields", "lbm_get_state",
                  "lbm_set_state", "lbm_diag", "lbm_synchronize"):
         getattr(L, name).restype = ctypes.c_int
@@ -100,6 +102,19 @@ def make_params(stream=None, **kw) -> lbm_params:
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     return lbm_params(stream=stream or None, **d)
+
+
+def diag_fields_noalloc(d_fields: int, n: int, d_out: int, stream=None) -> None:
+    """lbm_diag_fields_noalloc: reduce caller-owned device fields (5*n doubles,
+    planes phi, rho, ux, uy, p) into 4 device doubles at d_out without any
+    allocation.  d_fields/d_out are device addresses (e.g. tensor.data_ptr())."""
+    L = load()
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    err = ctypes.create_string_buffer(256)
+    rc = L.lbm_diag_fields_noalloc(d_fields, n, d_out, stream or None, err, len(err))
+    if rc != LBM_OK:
+        raise LbmError(rc, err.value.decode())
 
 
 def _dptr(a):
