@@ -57,6 +57,13 @@ enum {
     LBM_NORMAL_LOCAL = 1    /* n from the non-equilibrium of f_i           (Eq. 29) */
 };
 enum { LBM_STORE_FP32 = 0 };
+/* step kernel (kernel); both compute the same arithmetic */
+enum {
+    LBM_KERNEL_AUTO = 0,    /* the faster on GB300: currently LBM_KERNEL_GENERIC */
+    LBM_KERNEL_GENERIC = 1, /* 32 x 8 tiles, one thread per node, direct loads; any grid */
+    LBM_KERNEL_TMA = 2      /* persistent, tiles staged by bulk tensor copies; nx % 4 == 0,
+                               nx >= 72, ny >= 20 */
+};
 
 typedef struct {
     double rho_l, rho_g;  /* liquid / gas densities, Eq. 13; rho_g > 0 */
@@ -74,6 +81,7 @@ typedef struct {
                              stream and returns LBM_ERR_NONFINITE if any node produced
                              a non-finite phi, u or p since the last check; 0: off */
     void* stream;         /* cudaStream_t for all work; NULL = default stream */
+    int kernel;           /* LBM_KERNEL_* */
 } lbm_params;
 
 /*

@@ -58,7 +58,10 @@ struct Nbr {
     bool lo, hi;      // node touches the wall at y = -1/2 / y = ny - 1/2
 };
 
+// WALLS < 0: decided at run time from `walls`; 0/1: fixed at compile time.
+template <int WALLS = -1>
 __device__ __forceinline__ Nbr make_nbr(int x, int y, int nx, int ny, int walls) {
+    if (WALLS >= 0) walls = WALLS;
     Nbr q;
     q.x = x;
     q.xm = (x == 0) ? nx - 1 : x - 1;
@@ -89,10 +92,51 @@ __device__ __forceinline__ void pull9(const float* __restrict__ s, size_t N, con
     v[8] = q.hi ? __ldg(s + 6 * N + q.r0 + q.x) : __ldg(s + 8 * N + q.rp + q.xm);
 }
 
+// Explicitly rounded FP32 operations.  All arithmetic of the step goes
+// through these, so no multiply-add contraction is left to the compiler and
+// every kernel that inlines the functions below (direct-load, TMA-staged,
+// field read-back, initialisation) produces the same bits for the same
+// inputs.  IEEE division and square root throughout.
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+// Hardware reciprocal and reciprocal square root (one instruction each,
+// relative error below 2^-22; operands here are never subnormal: rho >= rho_g,
+// tau_g >= 1/2, |grad phi|^2 > 1e-12).  Deterministic, so every kernel still
+// produces the same bits.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// c_i . v for the nine directions of Eq. 10; opposite directions get exactly
+// opposite values (one rounding per pair).
+__device__ __forceinline__ void cdot9(float vx, float vy, float c[9]) {
+    const float s = add(vx, vy), d = sub(vy, vx);
+    c[0] = 0.f;
+    c[1] = vx;
+    c[2] = vy;
+    c[3] = -vx;
+    c[4] = -vy;
+    c[5] = s;
+    c[6] = d;
+    c[7] = -s;
+    c[8] = -d;
+}
+
 // phi = sum_i f_i (Eq. 12), in one fixed association order everywhere so a
 // node's phi is bit-identical whichever block computes it.
 __device__ __forceinline__ float sum9(const float v[9]) {
-    return ((v[0] + (v[1] + v[3])) + (v[2] + v[4])) + ((v[5] + v[7]) + (v[6] + v[8]));
+    return add(add(add(v[0], add(v[1], v[3])), add(v[2], v[4])),
+               add(add(v[5], v[7]), add(v[6], v[8])));
 }
 
 // coordinate of a tile/halo slot folded into the grid: periodic wrap in x;
@@ -109,40 +153,45 @@ __device__ __forceinline__ int fold_y(int y, int ny, int walls) {
     return y;
 }
 
+template <int WALLS = -1>
 __device__ __forceinline__ float phi_at(const float* __restrict__ fs, size_t N, int x, int y,
                                         int nx, int ny, int walls) {
     float v[9];
-    pull9(fs, N, make_nbr(x, y, nx, ny, walls), v);
+    pull9(fs, N, make_nbr<WALLS>(x, y, nx, ny, walls), v);
     return sum9(v);
 }
 
-// nu(phi) by Eq. 24, 25 or 26
-__device__ __forceinline__ float viscosity(const Model& m, float phi, float rho) {
-    if (m.visc_mode == 1) return 1.f / fmaf(phi, m.inv_nu_l - m.inv_nu_g, m.inv_nu_g);
-    if (m.visc_mode == 2) return (phi >= 0.5f ? m.mu_l : m.mu_g) / rho;
-    return fmaf(phi, m.nu_l - m.nu_g, m.nu_g);
+// nu(phi) by Eq. 24, 25 or 26 (inv_rho = 1/rho(phi) for Eq. 26)
+__device__ __forceinline__ float viscosity(const Model& m, float phi, float inv_rho) {
+    if (m.visc_mode == 1) return rcp_approx(fma_rn(phi, sub(m.inv_nu_l, m.inv_nu_g), m.inv_nu_g));
+    if (m.visc_mode == 2) return mul(phi >= 0.5f ? m.mu_l : m.mu_g, inv_rho);
+    return fma_rn(phi, sub(m.nu_l, m.nu_g), m.nu_g);
 }
 
 // Macroscopic state of one node from its pulled g_i and the phi stencil.
 struct Macro {
-    float rho, Fx, Fy, ux, uy, p;
+    float rho, inv_rho, Fx, Fy, ux, uy, p, usq;
 };
 
 __device__ __forceinline__ Macro macroscopic(const Model& m, const float g[9], float phi,
                                              float gx, float gy, float lap) {
     Macro o;
-    o.rho = fmaf(phi, m.drho, m.rho_g);                                     // Eq. 13
-    const float mu = m.beta4 * phi * (phi - 1.f) * (phi - 0.5f) - m.kappa * lap; // Eq. 6
-    o.Fx = fmaf(mu, gx, m.Gx);                                              // Eqs. 5, 19
-    o.Fy = fmaf(mu, gy, m.Gy);
-    const float mx = (g[1] - g[3]) + ((g[5] - g[6]) + (g[8] - g[7]));
-    const float my = (g[2] - g[4]) + ((g[5] - g[8]) + (g[6] - g[7]));
-    o.ux = (mx + 0.5f * o.Fx) / o.rho;                                      // Eq. 22a
-    o.uy = (my + 0.5f * o.Fy) / o.rho;
-    const float snz = ((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
-    const float usq = o.ux * o.ux + o.uy * o.uy;
+    o.rho = fma_rn(phi, m.drho, m.rho_g);                                      // Eq. 13
+    const float bulk = mul(mul(mul(m.beta4, phi), sub(phi, 1.f)), sub(phi, 0.5f));
+    const float mu = fma_rn(-m.kappa, lap, bulk);                              // Eq. 6
+    o.Fx = fma_rn(mu, gx, m.Gx);                                               // Eqs. 5, 19
+    o.Fy = fma_rn(mu, gy, m.Gy);
+    const float mx = add(sub(g[1], g[3]), add(sub(g[5], g[6]), sub(g[8], g[7])));
+    const float my = add(sub(g[2], g[4]), add(sub(g[5], g[8]), sub(g[6], g[7])));
+    o.inv_rho = rcp_approx(o.rho);
+    o.ux = mul(fma_rn(0.5f, o.Fx, mx), o.inv_rho);                            // Eq. 22a
+    o.uy = mul(fma_rn(0.5f, o.Fy, my), o.inv_rho);
+    const float snz = add(add(add(g[1], g[3]), add(g[2], g[4])), add(add(g[5], g[7]), add(g[6], g[8])));
+    o.usq = fma_rn(o.ux, o.ux, mul(o.uy, o.uy));
     // Eq. 22b with c_s^2/(1 - w_0) = 3/5 and rho s_0(u) = -(2/3) rho |u|^2
-    o.p = 0.6f * (snz + 0.5f * m.drho * (o.ux * gx + o.uy * gy) - (2.f / 3.f) * o.rho * usq);
+    const float ugrad = fma_rn(o.ux, gx, mul(o.uy, gy));
+    const float t = fma_rn(mul(0.5f, m.drho), ugrad, snz);
+    o.p = mul(0.6f, fma_rn(mul(-2.f / 3.f, o.rho), o.usq, t));
     return o;
 }
 
@@ -154,15 +203,32 @@ struct Stencil {
 __device__ __forceinline__ Stencil stencil(float pC, float pE, float pW, float pN, float pS,
                                            float pNE, float pNW, float pSW, float pSE) {
     Stencil s;
-    const float dd = (pNE - pSW);
-    const float da = (pSE - pNW);
-    s.gx = (pE - pW) * (1.f / 3.f) + (dd + da) * (1.f / 12.f);
-    s.gy = (pN - pS) * (1.f / 3.f) + (dd - da) * (1.f / 12.f);
+    const float dd = sub(pNE, pSW);
+    const float da = sub(pSE, pNW);
+    s.gx = fma_rn(sub(pE, pW), 1.f / 3.f, mul(add(dd, da), 1.f / 12.f));
+    s.gy = fma_rn(sub(pN, pS), 1.f / 3.f, mul(sub(dd, da), 1.f / 12.f));
     // differences to the centre first: nearly exact in FP32 for neighbouring
     // values (Sterbenz), so the Laplacian carries no O(ulp(phi)) cancellation
-    s.lap = (((pE - pC) + (pW - pC)) + ((pN - pC) + (pS - pC))) * (2.f / 3.f) +
-            (((pNE - pC) + (pSW - pC)) + ((pNW - pC) + (pSE - pC))) * (1.f / 6.f);
+    const float axis = add(add(sub(pE, pC), sub(pW, pC)), add(sub(pN, pC), sub(pS, pC)));
+    const float diag = add(add(sub(pNE, pC), sub(pSW, pC)), add(sub(pNW, pC), sub(pSE, pC)));
+    s.lap = fma_rn(axis, 2.f / 3.f, mul(diag, 1.f / 6.f));
     return s;
+}
+
+// f_i^eq (Eq. 9) formed as w phi + 3 w phi (c_i.u): opposite directions round
+// symmetrically about the representable w phi, so each pair sums to 2 w phi
+// exactly (writing w phi (1 +- 3 c.u) rounds 1+x and 1-x on different grids
+// and drifts sum phi).
+__device__ __forceinline__ float feq_i(int i, float phi, float cu) {
+    const float wphi = mul(w_of(i), phi);
+    return fma_rn(mul(3.f, wphi), cu, wphi);
+}
+
+// g_i^eq (Eqs. 16, 17): p/c_s^2 (w_i - [i == 0]) + rho w_i (3 cu + 4.5 cu^2 - 1.5 |u|^2)
+__device__ __forceinline__ float geq_i(int i, float p3, float rho, float cu, float usq) {
+    const float w = w_of(i);
+    const float s = mul(w, fma_rn(cu, fma_rn(4.5f, cu, 3.f), mul(-1.5f, usq)));
+    return fma_rn(rho, s, mul(p3, i == 0 ? w - 1.f : w));
 }
 
 // Both collisions of one node (Eqs. 2, 3, 8, 9, 11 and 15-17, 20); f and g are
@@ -171,68 +237,61 @@ __device__ __forceinline__ Stencil stencil(float pC, float pE, float pW, float p
 __device__ __forceinline__ float2 collide(const Model& m, float f[9], float g[9], float phi,
                                           const Stencil& st, const Macro& M, float2 phiu_prev) {
     const float ux = M.ux, uy = M.uy;
-    const float usq = ux * ux + uy * uy;
     // relaxation time of the flow field, Eq. 23
-    const float nu = viscosity(m, phi, M.rho);
-    const float omega_g = 1.f / fmaf(3.f, nu, 0.5f);
-    const float src_g = fmaf(-0.5f, omega_g, 1.f);
+    const float nu = viscosity(m, phi, M.inv_rho);
+    const float omega_g = rcp_approx(fma_rn(3.f, nu, 0.5f));
+    const float src_g = fma_rn(-0.5f, omega_g, 1.f);
+
+    float cu[9];
+    cdot9(ux, uy, cu);
+    float fe[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fe[i] = feq_i(i, phi, cu[i]);
 
     // d_t(phi u) by the backward difference, Eq. 11
-    const float2 phiu = make_float2(phi * ux, phi * uy);
-    const float Dx = phiu.x - phiu_prev.x;
-    const float Dy = phiu.y - phiu_prev.y;
-    const float lam = m.four_over_W * phi * (1.f - phi); // Eq. 3
+    const float2 phiu = make_float2(mul(phi, ux), mul(phi, uy));
+    const float Dx = sub(phiu.x, phiu_prev.x);
+    const float Dy = sub(phiu.y, phiu_prev.y);
+    const float lam = mul(mul(m.four_over_W, phi), sub(1.f, phi));  // Eq. 3
     float nx_ = 0.f, ny_ = 0.f;
     if (!m.local_normal) {  // Eq. 2 with the gradient of Eq. 27
-        const float g2 = st.gx * st.gx + st.gy * st.gy;
+        const float g2 = fma_rn(st.gx, st.gx, mul(st.gy, st.gy));
         if (g2 > 1e-12f) {  // |grad phi| > 1e-6: n is 0/0 below FP32 resolution
-            const float inv = 1.f / sqrtf(g2);
-            nx_ = st.gx * inv;
-            ny_ = st.gy * inv;
+            const float inv = rsqrt_approx(g2);
+            nx_ = mul(st.gx, inv);
+            ny_ = mul(st.gy, inv);
         }
     } else {  // Eq. 29: C = sum c_i (f_i - f_i^eq) + d_t(phi u)/2, n = -C/|C|
-        float Cx = 0.5f * Dx, Cy = 0.5f * Dy;
+        float ne[9];
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const float cu = cx_of(i) * ux + cy_of(i) * uy;
-            const float wphi = w_of(i) * phi;
-            const float neq = f[i] - fmaf(3.f * wphi, cu, wphi);
-            Cx += cx_of(i) * neq;
-            Cy += cy_of(i) * neq;
-        }
-        const float c2 = Cx * Cx + Cy * Cy;
+        for (int i = 1; i < 9; ++i) ne[i] = sub(f[i], fe[i]);
+        const float Cx = add(mul(0.5f, Dx), add(sub(ne[1], ne[3]), add(sub(ne[5], ne[6]), sub(ne[8], ne[7]))));
+        const float Cy = add(mul(0.5f, Dy), add(sub(ne[2], ne[4]), add(sub(ne[5], ne[8]), sub(ne[6], ne[7]))));
+        const float c2 = fma_rn(Cx, Cx, mul(Cy, Cy));
         if (c2 > 1e-12f) {
-            const float inv = 1.f / sqrtf(c2);
-            nx_ = -Cx * inv;
-            ny_ = -Cy * inv;
+            const float inv = rsqrt_approx(c2);
+            nx_ = -mul(Cx, inv);
+            ny_ = -mul(Cy, inv);
         }
     }
     // F_i = (1 - 1/2tau_f) w_i 3 c_i . (D + lambda n / 3)           Eq. 11
-    const float ax = fmaf(lam * (1.f / 3.f), nx_, Dx);
-    const float ay = fmaf(lam * (1.f / 3.f), ny_, Dy);
-    const float p3 = 3.f * M.p;
-    const float hx = 3.f * M.Fx, hy = 3.f * M.Fy;              // 3 F
-    const float ex = 3.f * m.drho * st.gx, ey = 3.f * m.drho * st.gy;
+    const float l3 = mul(lam, 1.f / 3.f);
+    float ca[9], ch[9], ce[9];
+    cdot9(fma_rn(l3, nx_, Dx), fma_rn(l3, ny_, Dy), ca);
+    cdot9(mul(3.f, M.Fx), mul(3.f, M.Fy), ch);                    // c_i . 3F
+    const float e3 = mul(3.f, m.drho);
+    cdot9(mul(e3, st.gx), mul(e3, st.gy), ce);                    // c_i . 3 (rho_l - rho_g) grad phi
+    const float p3 = mul(3.f, M.p);
 
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const float w = w_of(i);
-        const float cu = cx_of(i) * ux + cy_of(i) * uy;
-        // Allen-Cahn: f_i^eq (Eq. 9) as w phi + 3 w phi (c_i.u): opposite
-        // directions round symmetrically about the representable w phi, so
-        // the pair sums to 2 w phi exactly (no drift of sum phi from 1 +- x
-        // rounding on the two grids around 1.0), then source (Eq. 11), BGK (Eq. 8)
-        const float wphi = w * phi;
-        const float feq = fmaf(3.f * wphi, cu, wphi);
-        const float Fi = m.src_f * 3.f * w * (cx_of(i) * ax + cy_of(i) * ay);
-        f[i] = fmaf(m.inv_tau_f, feq - f[i], f[i]) + Fi;
+        // Allen-Cahn: source (Eq. 11), BGK (Eq. 8)
+        const float Fi = mul(mul(m.src_f, 3.f * w_of(i)), ca[i]);
+        f[i] = add(fma_rn(m.inv_tau_f, sub(fe[i], f[i]), f[i]), Fi);
         // Navier-Stokes: g_i^eq (Eqs. 16, 17), forcing (Eq. 20), BGK (Eq. 15)
-        const float s = w * (cu * fmaf(4.5f, cu, 3.f) - 1.5f * usq);
-        const float geq = (i == 0 ? p3 * (w - 1.f) : p3 * w) + M.rho * s;
-        const float cF = cx_of(i) * hx + cy_of(i) * hy;
-        const float cg = cx_of(i) * ex + cy_of(i) * ey;
-        const float Gi = src_g * w * fmaf(cu, cg, cF);
-        g[i] = fmaf(omega_g, geq - g[i], g[i]) + Gi;
+        const float geq = geq_i(i, p3, M.rho, cu[i], M.usq);
+        const float Gi = mul(mul(src_g, w_of(i)), fma_rn(cu[i], ce[i], ch[i]));
+        g[i] = add(fma_rn(omega_g, sub(geq, g[i]), g[i]), Gi);
     }
     return phiu;
 }

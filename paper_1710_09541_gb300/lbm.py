@@ -26,6 +26,7 @@ LBM_VISC_LINEAR_NU, LBM_VISC_INVERSE_NU, LBM_VISC_STEP_MU = 0, 1, 2
 LBM_BC_PERIODIC, LBM_BC_WALLS = 0, 1
 LBM_NORMAL_CENTRAL, LBM_NORMAL_LOCAL = 0, 1
 LBM_STORE_FP32 = 0
+LBM_KERNEL_AUTO, LBM_KERNEL_GENERIC, LBM_KERNEL_TMA = 0, 1, 2
 
 # every entry point include/lbm_pf.h declares
 EXPORTS = ("lbm_create", "lbm_init", "lbm_step", "lbm_get_fields", "lbm_state_bytes",
@@ -50,6 +51,7 @@ class lbm_params(ctypes.Structure):
         ("bc_y", ctypes.c_int), ("normal_scheme", ctypes.c_int),
         ("storage", ctypes.c_int), ("check_every", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("kernel", ctypes.c_int),
     ]
 
 
@@ -94,7 +96,8 @@ def make_params(stream=None, **kw) -> lbm_params:
     an integer cudaStream_t, an object with ``cuda_stream`` (torch.cuda.Stream)
     or None for the default stream."""
     d = dict(rho_l=1.0, rho_g=1e-3, nu_l=0.1, nu_g=0.1, visc_mode=0, sigma=0.01, W=4.0,
-             tau_h=0.8, Gx=0.0, Gy=0.0, bc_y=0, normal_scheme=0, storage=0, check_every=0)
+             tau_h=0.8, Gx=0.0, Gy=0.0, bc_y=0, normal_scheme=0, storage=0, check_every=0,
+             kernel=0)
     unknown = set(kw) - set(d)
     if unknown:
         raise TypeError(f"unknown parameters: {sorted(unknown)}")
