@@ -79,17 +79,18 @@ __device__ __forceinline__ Nbr make_nbr(int x, int y, int nx, int ny, int walls)
 // Pull (stream) the 9 populations of one node from buffer s:
 // v_i = s_i(x - c_i); a link that crosses a wall returns the node's own
 // post-collision value of the opposite direction (half-way bounce-back).
-__device__ __forceinline__ void pull9(const float* __restrict__ s, size_t N, const Nbr& q,
+__device__ __forceinline__ void pull9(const float* __restrict__ s, size_t Nz, const Nbr& q,
                                       float v[9]) {
-    v[0] = __ldg(s + q.r0 + q.x);
-    v[1] = __ldg(s + N + q.r0 + q.xm);
-    v[3] = __ldg(s + 3 * N + q.r0 + q.xp);
-    v[2] = q.lo ? __ldg(s + 4 * N + q.r0 + q.x) : __ldg(s + 2 * N + q.rm + q.x);
-    v[4] = q.hi ? __ldg(s + 2 * N + q.r0 + q.x) : __ldg(s + 4 * N + q.rp + q.x);
-    v[5] = q.lo ? __ldg(s + 7 * N + q.r0 + q.x) : __ldg(s + 5 * N + q.rm + q.xm);
-    v[6] = q.lo ? __ldg(s + 8 * N + q.r0 + q.x) : __ldg(s + 6 * N + q.rm + q.xp);
-    v[7] = q.hi ? __ldg(s + 5 * N + q.r0 + q.x) : __ldg(s + 7 * N + q.rp + q.xp);
-    v[8] = q.hi ? __ldg(s + 6 * N + q.r0 + q.x) : __ldg(s + 8 * N + q.rp + q.xm);
+    const int N = (int)Nz;  // 20 N < 2^31 (checked at create): 32-bit offsets
+    v[0] = __ldg(s + (q.r0 + q.x));
+    v[1] = __ldg(s + (N + q.r0 + q.xm));
+    v[3] = __ldg(s + (3 * N + q.r0 + q.xp));
+    v[2] = q.lo ? __ldg(s + (4 * N + q.r0 + q.x)) : __ldg(s + (2 * N + q.rm + q.x));
+    v[4] = q.hi ? __ldg(s + (2 * N + q.r0 + q.x)) : __ldg(s + (4 * N + q.rp + q.x));
+    v[5] = q.lo ? __ldg(s + (7 * N + q.r0 + q.x)) : __ldg(s + (5 * N + q.rm + q.xm));
+    v[6] = q.lo ? __ldg(s + (8 * N + q.r0 + q.x)) : __ldg(s + (6 * N + q.rm + q.xp));
+    v[7] = q.hi ? __ldg(s + (5 * N + q.r0 + q.x)) : __ldg(s + (7 * N + q.rp + q.xp));
+    v[8] = q.hi ? __ldg(s + (6 * N + q.r0 + q.x)) : __ldg(s + (8 * N + q.rp + q.xm));
 }
 
 // Explicitly rounded FP32 operations.  All arithmetic of the step goes
@@ -245,8 +246,9 @@ __device__ __forceinline__ float2 collide(const Model& m, float f[9], float g[9]
     float cu[9];
     cdot9(ux, uy, cu);
     float fe[9];
+    fe[0] = mul(w_of(0), phi);  // f_0^eq = w_0 phi (c_0 = 0)
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fe[i] = feq_i(i, phi, cu[i]);
+    for (int i = 1; i < 9; ++i) fe[i] = feq_i(i, phi, cu[i]);
 
     // d_t(phi u) by the backward difference, Eq. 11
     const float2 phiu = make_float2(mul(phi, ux), mul(phi, uy));
@@ -283,8 +285,17 @@ __device__ __forceinline__ float2 collide(const Model& m, float f[9], float g[9]
     cdot9(mul(e3, st.gx), mul(e3, st.gy), ce);                    // c_i . 3 (rho_l - rho_g) grad phi
     const float p3 = mul(3.f, M.p);
 
+    // i = 0 (c_0 = 0): F_0 = G_0 = 0 and the velocity-linear parts vanish;
+    // written out because the explicitly rounded operations cannot fold the
+    // products with zero away.  The results are the same bits as the general
+    // form below would give.
+    f[0] = fma_rn(m.inv_tau_f, sub(fe[0], f[0]), f[0]);
+    {
+        const float geq0 = fma_rn(M.rho, mul(w_of(0), mul(-1.5f, M.usq)), mul(p3, w_of(0) - 1.f));
+        g[0] = fma_rn(omega_g, sub(geq0, g[0]), g[0]);
+    }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
+    for (int i = 1; i < 9; ++i) {
         // Allen-Cahn: source (Eq. 11), BGK (Eq. 8)
         const float Fi = mul(mul(m.src_f, 3.f * w_of(i)), ca[i]);
         f[i] = add(fma_rn(m.inv_tau_f, sub(fe[i], f[i]), f[i]), Fi);

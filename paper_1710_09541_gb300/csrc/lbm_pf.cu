@@ -116,14 +116,15 @@ __global__ void __launch_bounds__(TX* TY, LBM_STEP_MINB)
     // one test: a NaN or Inf in any of phi, u, p makes the sum non-finite
     if (!isfinite(add(add(phi, M.ux), add(M.uy, M.p)))) atomicOr(flag, 1u);
 
-    const float2 prev = make_float2(phiu[n], phiu[N + n]);
+    const int N32 = (int)N, n32 = (int)n;  // 20 N < 2^31: 32-bit offsets
+    const float2 prev = make_float2(phiu[n32], phiu[N32 + n32]);
     const float2 now = collide(m, f, g, phi, st, M, prev);
-    phiu[n] = now.x;
-    phiu[N + n] = now.y;
+    phiu[n32] = now.x;
+    phiu[N32 + n32] = now.y;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        fd[i * N + n] = f[i];
-        gd[i * N + n] = g[i];
+        fd[i * N32 + n32] = f[i];
+        gd[i * N32 + n32] = g[i];
     }
 }
 
