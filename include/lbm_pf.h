@@ -56,7 +56,14 @@ enum {
     LBM_NORMAL_CENTRAL = 0, /* n = grad phi / |grad phi|, grad by Eq. 27  (Eq. 2) */
     LBM_NORMAL_LOCAL = 1    /* n from the non-equilibrium of f_i           (Eq. 29) */
 };
-enum { LBM_STORE_FP32 = 0 };
+/* population storage in HBM (storage); arithmetic is FP32 in every format */
+enum {
+    LBM_STORE_FP32 = 0,         /* f, g: 9 FP32 planes each (72 B/node) */
+    LBM_STORE_FP16_SHIFTED = 1, /* f_0 FP32 (takes the rounding of the others, so sum phi is
+                                   conserved); f_1..8 FP16 of f_i/w_i - 1/2; g FP16 of
+                                   2^10 g_i/w_i (38 B/node) */
+    LBM_STORE_BF16_SHIFTED = 2  /* as FP16_SHIFTED with BF16 and g unscaled */
+};
 /* step kernel (kernel); both compute the same arithmetic */
 enum {
     LBM_KERNEL_AUTO = 0,    /* the faster on GB300: currently LBM_KERNEL_GENERIC */
@@ -76,7 +83,7 @@ typedef struct {
     double Gx, Gy;        /* body-force density G (Eqs. 4b, 19), same in both phases */
     int bc_y;             /* LBM_BC_PERIODIC or LBM_BC_WALLS */
     int normal_scheme;    /* LBM_NORMAL_* */
-    int storage;          /* LBM_STORE_FP32 (populations stored as FP32) */
+    int storage;          /* LBM_STORE_*: how populations are stored between steps */
     int check_every;      /* > 0: every check_every steps lbm_step synchronises the
                              stream and returns LBM_ERR_NONFINITE if any node produced
                              a non-finite phi, u or p since the last check; 0: off */

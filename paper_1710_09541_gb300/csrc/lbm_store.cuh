@@ -1,0 +1,200 @@
+// lbm_store.cuh -- population storage formats.  All arithmetic is FP32; the
+// formats differ only in how the two population sets sit in HBM.
+//
+//   FP32 (LBM_STORE_FP32): f and g as 9 FP32 planes each (36 B + 36 B / node);
+//     f_0 is written as phi - sum_{i>0} f_i (see below).
+//
+//   FP16 / BF16 shifted (LBM_STORE_FP16_SHIFTED, LBM_STORE_BF16_SHIFTED):
+//     f_0          FP32 plane, written as phi - sum_{i>0} decode(encode(f_i)):
+//                  the rest population absorbs the rounding of the eight
+//                  moving ones, so the stored populations of a node sum to its
+//                  phi up to FP32 round-off and sum phi stays conserved.
+//     f_1..f_8     16-bit planes of f_i / w_i - 1/2: the offset from the
+//                  weight-scaled rest state at phi_ref = 1/2 (phi lies in [0, 1]).
+//     g_0..g_8     16-bit planes of S g_i / w_i (p_ref = 0), with S = 2^10 for
+//                  FP16 so pressures and momenta of O(1e-6) stay above the
+//                  FP16 subnormal range; S = 1 for BF16 (FP32 exponent range).
+//   Bytes per node: f 4 + 16, g 18 (92 B read + written per update with phi u).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbm_kernels.cuh"
+
+namespace lbmpf {
+
+enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2 };
+
+template <int ST>
+struct Pop;
+
+template <>
+struct Pop<ST_FP32> {
+    static size_t f_bytes(size_t N) { return 36 * N; }
+    static size_t g_bytes(size_t N) { return 36 * N; }
+    __device__ static float ldf(const void* b, int N, int i, int idx) {
+        return __ldg(static_cast<const float*>(b) + (i * N + idx));
+    }
+    __device__ static float ldg(const void* b, int N, int i, int idx) { return ldf(b, N, i, idx); }
+    // store the post-collision set of node idx; f_0 is written as the
+    // remainder phi - sum_{i>0} f_i, so the stored populations of a node sum
+    // to its phi up to one rounding and sum phi does not drift with the
+    // rounding of the collision
+    __device__ static void stf(void* b, int N, int idx, const float f[9], float phi) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i) static_cast<float*>(b)[i * N + idx] = f[i];
+        static_cast<float*>(b)[idx] =
+            sub(phi, add(add(add(f[1], f[3]), add(f[2], f[4])), add(add(f[5], f[7]), add(f[6], f[8]))));
+    }
+    __device__ static void stg(void* b, int N, int idx, const float g[9]) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) static_cast<float*>(b)[i * N + idx] = g[i];
+    }
+    // both sets, stores of f_i and g_i interleaved (as measured fastest)
+    __device__ static void stfg(void* fb, void* gb, int N, int idx, const float f[9],
+                                const float g[9], float phi) {
+        float* F = static_cast<float*>(fb);
+        float* G = static_cast<float*>(gb);
+        F[idx] = sub(phi, add(add(add(f[1], f[3]), add(f[2], f[4])), add(add(f[5], f[7]), add(f[6], f[8]))));
+        G[idx] = g[0];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            F[i * N + idx] = f[i];
+            G[i * N + idx] = g[i];
+        }
+    }
+    // one plane entry (checkpoint and initial-state permutations); the rest
+    // population's correction is zero in FP32
+    __device__ static void putf(void* b, int N, int i, int idx, float v) {
+        static_cast<float*>(b)[i * N + idx] = v;
+    }
+    __device__ static void putg(void* b, int N, int i, int idx, float v) {
+        static_cast<float*>(b)[i * N + idx] = v;
+    }
+    __device__ static float round_f(int, float v) { return v; }
+};
+
+template <typename H>
+struct Half16;
+template <>
+struct Half16<__half> {
+    static constexpr float GS = 1024.f;
+    __device__ static float to_f(unsigned short u) { return __half2float(__ushort_as_half(u)); }
+    __device__ static unsigned short from_f(float v) { return __half_as_ushort(__float2half_rn(v)); }
+};
+template <>
+struct Half16<__nv_bfloat16> {
+    static constexpr float GS = 1.f;
+    __device__ static float to_f(unsigned short u) { return __bfloat162float(__ushort_as_bfloat16(u)); }
+    __device__ static unsigned short from_f(float v) {
+        return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    }
+};
+
+template <typename H>
+struct Shifted16 {
+    using C = Half16<H>;
+    static size_t f_bytes(size_t N) { return 4 * N + 16 * N; }
+    static size_t g_bytes(size_t N) { return 18 * N; }
+    __device__ static const unsigned short* fh(const void* b, int N) {
+        return reinterpret_cast<const unsigned short*>(static_cast<const float*>(b) + N);
+    }
+    __device__ static unsigned short* fh(void* b, int N) {
+        return reinterpret_cast<unsigned short*>(static_cast<float*>(b) + N);
+    }
+    // f_i = w_i (v + 1/2) for i > 0
+    __device__ static float dec_f(int i, unsigned short u) {
+        return fma_rn(C::to_f(u), w_of(i), 0.5f * w_of(i));
+    }
+    __device__ static unsigned short enc_f(int i, float v) {
+        return C::from_f(fma_rn(v, 1.f / w_of(i), -0.5f));
+    }
+    __device__ static float dec_g(int i, unsigned short u) {
+        return mul(C::to_f(u), w_of(i) / C::GS);
+    }
+    __device__ static unsigned short enc_g(int i, float v) {
+        return C::from_f(mul(v, C::GS / w_of(i)));
+    }
+    __device__ static float ldf(const void* b, int N, int i, int idx) {
+        if (i == 0) return __ldg(static_cast<const float*>(b) + idx);
+        return dec_f(i, __ldg(fh(b, N) + ((i - 1) * N + idx)));
+    }
+    __device__ static float ldg(const void* b, int N, int i, int idx) {
+        return dec_g(i, __ldg(static_cast<const unsigned short*>(b) + (i * N + idx)));
+    }
+    __device__ static void stf(void* b, int N, int idx, const float f[9], float phi) {
+        float d[9];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const unsigned short e = enc_f(i, f[i]);
+            fh(b, N)[(i - 1) * N + idx] = e;
+            d[i] = dec_f(i, e);
+        }
+        static_cast<float*>(b)[idx] =
+            sub(phi, add(add(add(d[1], d[3]), add(d[2], d[4])), add(add(d[5], d[7]), add(d[6], d[8]))));
+    }
+    __device__ static void stg(void* b, int N, int idx, const float g[9]) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) static_cast<unsigned short*>(b)[i * N + idx] = enc_g(i, g[i]);
+    }
+    __device__ static void stfg(void* fb, void* gb, int N, int idx, const float f[9],
+                                const float g[9], float phi) {
+        stf(fb, N, idx, f, phi);
+        stg(gb, N, idx, g);
+    }
+    __device__ static void putf(void* b, int N, int i, int idx, float v) {
+        if (i == 0)
+            static_cast<float*>(b)[idx] = v;
+        else
+            fh(b, N)[(i - 1) * N + idx] = enc_f(i, v);
+    }
+    __device__ static void putg(void* b, int N, int i, int idx, float v) {
+        static_cast<unsigned short*>(b)[i * N + idx] = enc_g(i, v);
+    }
+    // the value a moving population takes after storage
+    __device__ static float round_f(int i, float v) { return i == 0 ? v : dec_f(i, enc_f(i, v)); }
+};
+
+template <>
+struct Pop<ST_FP16> : Shifted16<__half> {};
+template <>
+struct Pop<ST_BF16> : Shifted16<__nv_bfloat16> {};
+
+// Pull (stream) the 9 populations of node q through a storage format.
+template <int ST>
+__device__ __forceinline__ void pull9f(const void* s, int N, const Nbr& q, float v[9]) {
+    v[0] = Pop<ST>::ldf(s, N, 0, q.r0 + q.x);
+    v[1] = Pop<ST>::ldf(s, N, 1, q.r0 + q.xm);
+    v[3] = Pop<ST>::ldf(s, N, 3, q.r0 + q.xp);
+    v[2] = q.lo ? Pop<ST>::ldf(s, N, 4, q.r0 + q.x) : Pop<ST>::ldf(s, N, 2, q.rm + q.x);
+    v[4] = q.hi ? Pop<ST>::ldf(s, N, 2, q.r0 + q.x) : Pop<ST>::ldf(s, N, 4, q.rp + q.x);
+    v[5] = q.lo ? Pop<ST>::ldf(s, N, 7, q.r0 + q.x) : Pop<ST>::ldf(s, N, 5, q.rm + q.xm);
+    v[6] = q.lo ? Pop<ST>::ldf(s, N, 8, q.r0 + q.x) : Pop<ST>::ldf(s, N, 6, q.rm + q.xp);
+    v[7] = q.hi ? Pop<ST>::ldf(s, N, 5, q.r0 + q.x) : Pop<ST>::ldf(s, N, 7, q.rp + q.xp);
+    v[8] = q.hi ? Pop<ST>::ldf(s, N, 6, q.r0 + q.x) : Pop<ST>::ldf(s, N, 8, q.rp + q.xm);
+}
+template <int ST>
+__device__ __forceinline__ void pull9g(const void* s, int N, const Nbr& q, float v[9]) {
+    v[0] = Pop<ST>::ldg(s, N, 0, q.r0 + q.x);
+    v[1] = Pop<ST>::ldg(s, N, 1, q.r0 + q.xm);
+    v[3] = Pop<ST>::ldg(s, N, 3, q.r0 + q.xp);
+    v[2] = q.lo ? Pop<ST>::ldg(s, N, 4, q.r0 + q.x) : Pop<ST>::ldg(s, N, 2, q.rm + q.x);
+    v[4] = q.hi ? Pop<ST>::ldg(s, N, 2, q.r0 + q.x) : Pop<ST>::ldg(s, N, 4, q.rp + q.x);
+    v[5] = q.lo ? Pop<ST>::ldg(s, N, 7, q.r0 + q.x) : Pop<ST>::ldg(s, N, 5, q.rm + q.xm);
+    v[6] = q.lo ? Pop<ST>::ldg(s, N, 8, q.r0 + q.x) : Pop<ST>::ldg(s, N, 6, q.rm + q.xp);
+    v[7] = q.hi ? Pop<ST>::ldg(s, N, 5, q.r0 + q.x) : Pop<ST>::ldg(s, N, 7, q.rp + q.xp);
+    v[8] = q.hi ? Pop<ST>::ldg(s, N, 6, q.r0 + q.x) : Pop<ST>::ldg(s, N, 8, q.rp + q.xm);
+}
+
+template <int ST, int WALLS = -1>
+__device__ __forceinline__ float phi_at_st(const void* fs, int N, int x, int y, int nx, int ny,
+                                           int walls) {
+    float v[9];
+    if constexpr (ST == ST_FP32)  // the plain float pull (its address arithmetic measured faster)
+        pull9(static_cast<const float*>(fs), (size_t)N, make_nbr<WALLS>(x, y, nx, ny, walls), v);
+    else
+        pull9f<ST>(fs, N, make_nbr<WALLS>(x, y, nx, ny, walls), v);
+    return sum9(v);
+}
+
+}  // namespace lbmpf

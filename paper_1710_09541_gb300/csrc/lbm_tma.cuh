@@ -17,6 +17,7 @@
 #include <cuda.h>
 
 #include "lbm_kernels.cuh"
+#include "lbm_store.cuh"
 
 namespace lbmpf {
 
@@ -228,11 +229,7 @@ __global__ void __launch_bounds__(NT, 1)
             const size_t n = (size_t)y * nx + x;
             phiu[n] = now.x;
             phiu[N + n] = now.y;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                fd[i * N + n] = f[i];
-                gd[i * N + n] = g[i];
-            }
+            Pop<ST_FP32>::stfg(fd, gd, (int)N, (int)n, f, g, phi);
         }
         // the stage is read (and on edges written) through the generic proxy;
         // order that before the next bulk copy into it
