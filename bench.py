@@ -9,6 +9,12 @@ density ratio 1000, FP32 populations.  One step = one lattice time step of
 both distributions over the whole grid (one launch of the fused step kernel).
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank advances its
 own independent lattice (replicas; the method has no exchange between cases).
+
+The line also carries `batched`: 64 independent drop and impact cases of
+uneven sizes, Reynolds numbers and density ratios, advanced by the batched
+kernel with FP16-shifted storage, against the same cases run one by one on
+the plain FP32 single-case path; and `single_case_storage`: the 2048 x 2048
+workload with 16-bit storage.
 """
 from __future__ import annotations
 
@@ -166,6 +172,92 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+STORAGE_NAMES = {0: "fp32", 1: "fp16_shifted", 2: "bf16_shifted"}
+# FP16/BF16 shifted storage: f_0 FP32 (4 B) + f_1..8 and g_0..8 16-bit (34 B)
+# per set, read and written, plus (phi u): 2 * 38 + 16
+BYTES_PER_LU_SHIFTED16 = 92
+
+
+def _time_steps(torch, stream, fn):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def run_batched(torch, lbm, stream, steps, storage=1):
+    """The batched sweep: 64 independent drops and impacts of uneven sizes and
+    parameters, each advanced `steps` steps (a) one case after another on the
+    plain FP32 single-case path and (b) all together by the batched kernel with
+    the given storage; aggregate MLUPS of both, with the mass-conservation and
+    spurious-velocity figures of each run."""
+    specs = cases.batch_cases()
+    nodes = sum(sp["nx"] * sp["ny"] for sp in specs)
+
+    def make(st):
+        return [lbm.Lattice(sp["nx"], sp["ny"], stream=stream, storage=st, **sp["params"])
+                .init(sp["phi0"], sp["ux0"], sp["uy0"]) for sp in specs]
+
+    def accuracy(lats):
+        drift, umax = [], []
+        for sp, lat in zip(specs, lats):
+            d = lat.diag()
+            drift.append(abs(d[0] / sp["phi0"].sum() - 1.0))
+            umax.append(d[1])
+        return drift, umax
+
+    seq = make(0)
+    for lat in seq:
+        lat.step(5)
+    t_seq = _time_steps(torch, stream, lambda: [lat.step(steps) for lat in seq])
+    d_seq, u_seq = accuracy(seq)
+    for lat in seq:
+        lat.close()
+    bat = make(storage)
+    b = lbm.Batch(bat)
+    b.step(100)                                   # tile-shape tuning + warm-up
+    t_bat = _time_steps(torch, stream, lambda: b.step(steps))
+    shape, tuned_us, _ = b.info()
+    d_bat, u_bat = accuracy(bat)
+    b.close()
+    for lat in bat:
+        lat.close()
+    drops = [k for k, sp in enumerate(specs) if sp["kind"] == "static_drop"]
+    v_bat = nodes * steps / t_bat / 1e6
+    v_seq = nodes * steps / t_seq / 1e6
+    peak, _ = _peaks()
+    bpl = BYTES_PER_LU if storage == 0 else BYTES_PER_LU_SHIFTED16
+    return {
+        "cases": len(specs), "nodes": nodes, "steps_per_case": steps + 5,
+        "storage": STORAGE_NAMES[storage], "value": v_bat, "unit": UNIT,
+        "sequential_fp32": v_seq, "speedup_vs_sequential_fp32": v_bat / v_seq,
+        "tile": list(shape), "tuned_us_per_step": tuned_us, "bytes_per_lu": bpl,
+        "roofline_frac": v_bat * 1e6 * bpl / 1e9 / peak,
+        "sum_phi_rel_drift_max": {"batched": max(d_bat), "sequential_fp32": max(d_seq)},
+        "drop_umax_max": {"batched": max(u_bat[k] for k in drops),
+                          "sequential_fp32": max(u_seq[k] for k in drops)},
+        "launches_per_step": 1,
+    }
+
+
+def run_storage_variants(torch, lbm, stream, steps):
+    """Single-case MLUPS of the 2048 x 2048 workload with 16-bit storage."""
+    nx, ny = cases.PERF_NX, cases.PERF_NY
+    phi0, params = cases.perf_case()
+    out = {}
+    for st in (1, 2):
+        lat = lbm.Lattice(nx, ny, stream=stream, storage=st, **params).init(phi0)
+        lat.step(50)
+        t = _time_steps(torch, stream, lambda: lat.step(steps))
+        lat.close()
+        out[STORAGE_NAMES[st]] = {"value": nx * ny * steps / t / 1e6, "unit": UNIT,
+                                  "bytes_per_lu": BYTES_PER_LU_SHIFTED16, "steps": steps}
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -226,6 +318,11 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     lat.close()
 
+    batched = storage_variants = None
+    if not args.no_batched:
+        batched = run_batched(torch, lbm, stream, args.batch_steps)
+        storage_variants = run_storage_variants(torch, lbm, stream, 2000)
+
     times = torch.tensor([ms / 1e3, e2e_s], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(times, op=dist.ReduceOp.MAX)
@@ -261,6 +358,8 @@ def run_ours(args):
             "clocks": clk.summary(),
             "gpu_launches": args.steps,
             "sum_phi": s_phi, "umax": umax,
+            "batched": batched,
+            "single_case_storage": storage_variants,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -275,6 +374,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("bench.py: --warmup must be >= 3")

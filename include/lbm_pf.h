@@ -185,6 +185,37 @@ lbm_status lbm_diag(lbm_handle* h, double* sum_phi, double* umax, double* pmin,
 lbm_status lbm_diag_fields_noalloc(const double* d_fields, size_t n, double* d_out, void* stream,
                                    char* err, size_t err_len);
 
+/*
+ * Batched stepping of many independent cases: drops and impacts of uneven
+ * grid sizes, Reynolds numbers and density ratios advanced together.  A batch
+ * groups existing handles that share one device, one stream and one storage
+ * format; it does not own them (create, init, read back, checkpoint and
+ * destroy them as usual).  The paper runs one case at a time; batching is an
+ * addition of this library.
+ *
+ * lbm_batch_create -- build the batch over ncases handles (1 <= ncases <= 200,
+ *   each initialised, none repeated).  The batch keeps a tile table over all
+ *   cases and a private stream; handles must outlive the batch.
+ *   Errors: LBM_ERR_INVALID, LBM_ERR_OOM, LBM_ERR_CUDA (then *out == NULL).
+ * lbm_batch_step -- advance every case by nsteps time steps (the same update as
+ *   lbm_step, Sec. II, bit for bit).  One kernel launch per step covers the
+ *   tiles of all cases; steps run as replays of a CUDA graph of 32 steps.  The
+ *   first call with nsteps >= 100 times five tile shapes (32x4, 32x8, 32x16,
+ *   64x2, 64x4 nodes) on its own first 100 steps and keeps the fastest.
+ *   Ordered after earlier work on the cases' stream, and later work on that
+ *   stream waits for it.  A case may also be stepped on its own between batch
+ *   steps.
+ * lbm_batch_info -- tile shape in use, its measured microseconds per step
+ *   (0 before tuning) and whether tuning ran; any pointer may be NULL.
+ */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** out);
+lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
+lbm_status lbm_batch_info(const lbm_batch* b, int* tile_tx, int* tile_ty, double* us_per_step,
+                          int* tuned);
+void lbm_batch_destroy(lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+
 /* lbm_synchronize -- wait for all work enqueued by this handle. */
 lbm_status lbm_synchronize(lbm_handle* h);
 

@@ -135,6 +135,35 @@ def perf_case(nx=PERF_NX, ny=PERF_NY, seed=1):
     return spinodal(nx, ny, 0.5, 0.01, seed), params
 
 
+def batch_cases(n=64, seed=7):
+    """The batched sweep: n independent cases, half static drops (periodic) and
+    half droplet impacts (walls), on uneven grids from 256 x 256 to
+    1024 x 512 (multiples of 64), drop diameter D in [64, 160], film 0.1 D,
+    impact speed 0.04, Re log-uniform in [20, 500], density ratio in
+    {10, 100, 1000}.  Returns a list of dicts with nx, ny, kind, params,
+    phi0, ux0, uy0 (arrays float64 [ny, nx])."""
+    u = uniform01(seed, 6 * n).reshape(n, 6)
+    out = []
+    for c in range(n):
+        nx = 256 + 64 * int(u[c, 0] * 13)            # 256 .. 1024
+        ny = 256 + 64 * int(u[c, 1] * 5)             # 256 .. 512
+        D = float(min(64 + int(u[c, 2] * 97), 0.6 * min(nx, ny)))
+        ratio = (10.0, 100.0, 1000.0)[int(u[c, 3] * 3)]
+        Re = float(20.0 * (500.0 / 20.0) ** u[c, 4])
+        if c % 2 == 0:
+            params = params_static_drop(ratio=ratio)
+            phi0 = drop(nx, ny, D / 2, params["W"])
+            ux0 = uy0 = np.zeros_like(phi0)
+            kind = "static_drop"
+        else:
+            params = params_impact(D=D, U=0.04, Re=Re, We=8000.0, ratio=ratio, mu_ratio=40.0)
+            phi0, ux0, uy0 = impact(nx, ny, D, 0.1 * D, 0.04, params["W"])
+            kind = "impact"
+        out.append(dict(nx=nx, ny=ny, kind=kind, params=params, phi0=phi0, ux0=ux0, uy0=uy0,
+                        D=D, Re=Re, ratio=ratio))
+    return out
+
+
 def capillary_velocity(params):
     """sigma / mu_l: the velocity scale used to normalise velocity errors."""
     return params["sigma"] / (params["rho_l"] * params["nu_l"])
@@ -143,6 +172,6 @@ def capillary_velocity(params):
 __all__ = [
     "splitmix64", "uniform01", "drop", "layer", "spinodal", "impact",
     "params_static_drop", "params_poiseuille",
-    "params_spinodal", "params_impact", "perf_case", "capillary_velocity",
+    "params_spinodal", "params_impact", "perf_case", "batch_cases", "capillary_velocity",
     "PERF_NX", "PERF_NY",
 ]

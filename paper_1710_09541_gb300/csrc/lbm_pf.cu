@@ -9,6 +9,7 @@
 #include <cstring>
 #include <atomic>
 #include <new>
+#include <vector>
 
 #include <cudaTypedefs.h>
 
@@ -62,17 +63,18 @@ struct Ring {
 #ifndef LBM_STEP_MINB
 #define LBM_STEP_MINB 4
 #endif
+// One TX x TY tile with origin (x0, y0): the body shared by the single-case
+// step kernel and the batched persistent kernel (so both give the same bits).
 template <int TX, int TY, bool FIELDS, int WALLS, int ST>
-__global__ void __launch_bounds__(TX* TY, LBM_STEP_MINB)
-    k_step(const float* __restrict__ fs, const float* __restrict__ gs, float* __restrict__ fd,
-           float* __restrict__ gd, float* __restrict__ phiu, unsigned int* __restrict__ flag,
-           double* __restrict__ out, int nx, int ny, Model m) {
+__device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __restrict__ fs,
+                                          const float* __restrict__ gs, float* __restrict__ fd,
+                                          float* __restrict__ gd, float* __restrict__ phiu,
+                                          unsigned int* __restrict__ flag, double* __restrict__ out,
+                                          int nx, int ny, Model m, int x0, int y0) {
     if (WALLS >= 0) m.walls = WALLS;
-    __shared__ float sphi[TY + 2][TX + 2];
     const size_t N = (size_t)nx * ny;
     const int N32 = (int)N;  // 20 N < 2^31 (checked at create): 32-bit offsets
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = (x < nx) && (y < ny);
 
@@ -128,6 +130,16 @@ __global__ void __launch_bounds__(TX* TY, LBM_STEP_MINB)
     phiu[n32] = now.x;
     phiu[N32 + n32] = now.y;
     Pop<ST>::stfg(fd, gd, N32, n32, f, g, phi);
+}
+
+template <int TX, int TY, bool FIELDS, int WALLS, int ST>
+__global__ void __launch_bounds__(TX* TY, LBM_STEP_MINB)
+    k_step(const float* __restrict__ fs, const float* __restrict__ gs, float* __restrict__ fd,
+           float* __restrict__ gd, float* __restrict__ phiu, unsigned int* __restrict__ flag,
+           double* __restrict__ out, int nx, int ny, Model m) {
+    __shared__ float sphi[TY + 2][TX + 2];
+    step_tile<TX, TY, FIELDS, WALLS, ST>(sphi, fs, gs, fd, gd, phiu, flag, out, nx, ny, m,
+                                         blockIdx.x * TX, blockIdx.y * TY);
 }
 
 // ---------------------------------------------------------------------------
@@ -864,3 +876,354 @@ extern "C" lbm_status lbm_diag_fields_noalloc(const double* d_fields, size_t n, 
     }
     return LBM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched step: many independent cases (different sizes and parameters, one
+// storage format) advanced together.  One kernel launch covers a global list
+// of 32 x TY tiles over all cases, one block per tile (a tile table maps the
+// block to its case and tile); each tile runs the same step_tile body
+// as the single-case kernel, so a case advanced in a batch gives the same bits
+// as the case advanced alone.  Steps run as replays of a captured CUDA graph;
+// the tile height is picked by timing the candidates on the batch's own first
+// steps (all candidates give the same bits, so those steps count).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CaseDesc {
+    float* f[2];
+    float* g[2];
+    float* phiu;
+    unsigned int* flag;
+    int nx, ny;
+    int cur;  // buffer holding the current state when the batch parity is 0
+    int pad;
+    Model m;
+};
+
+// The whole case table travels as a kernel parameter (constant bank): the
+// block-uniform case data then needs no registers of the tile body.
+constexpr int BATCH_MAX_CASES = 200;
+struct BatchTable {
+    int ncases;
+    int tiles_x[BATCH_MAX_CASES];
+    int tile0[BATCH_MAX_CASES + 1];  // first tile of each case; tile0[ncases] = total
+    CaseDesc c[BATCH_MAX_CASES];
+};
+static_assert(sizeof(BatchTable) <= 32000, "kernel parameters are limited to 32 KB");
+
+// resident threads per SM the batch kernels are compiled for (sets the
+// register budget), and whether one body serves both boundary kinds
+#ifndef LBM_BATCH_THREADS
+#define LBM_BATCH_THREADS 1024
+#endif
+#ifndef LBM_BATCH_ONE_BODY
+#define LBM_BATCH_ONE_BODY 1
+#endif
+
+template <int TX, int TY, int ST>
+__global__ void __launch_bounds__(TX* TY, LBM_BATCH_THREADS / (TX * TY))
+    k_step_batch(const __grid_constant__ BatchTable T, int parity) {
+    __shared__ float sphi[TY + 2][TX + 2];
+    const int t = blockIdx.x;
+    int lo = 0, hi = T.ncases - 1;  // the case whose tiles contain block t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.tile0[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const CaseDesc& cd = T.c[lo];
+    const int lt = t - T.tile0[lo];
+    const int x0 = (lt % T.tiles_x[lo]) * TX, y0 = (lt / T.tiles_x[lo]) * TY;
+    const int c = (cd.cur + parity) & 1;
+#if LBM_BATCH_ONE_BODY
+    step_tile<TX, TY, false, -1, ST>(sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu,
+                                     cd.flag, nullptr, cd.nx, cd.ny, cd.m, x0, y0);
+#else
+    // uniform per block: the periodic or the walled specialisation
+    if (cd.m.walls)
+        step_tile<TX, TY, false, 1, ST>(sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu,
+                                        cd.flag, nullptr, cd.nx, cd.ny, cd.m, x0, y0);
+    else
+        step_tile<TX, TY, false, 0, ST>(sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu,
+                                        cd.flag, nullptr, cd.nx, cd.ny, cd.m, x0, y0);
+#endif
+}
+
+// tile shapes the tuner times (TX x TY nodes, one thread each)
+constexpr int BATCH_NCAND = 5;
+constexpr int BATCH_TX[BATCH_NCAND] = {32, 32, 32, 64, 64};
+constexpr int BATCH_TY[BATCH_NCAND] = {4, 8, 16, 2, 4};
+constexpr int BATCH_GRAPH_STEPS = 32;  // steps per graph replay (even)
+constexpr int BATCH_TUNE_WARM = 4, BATCH_TUNE_STEPS = 16;
+
+using BatchKernel = void (*)(BatchTable, int);
+
+template <int ST>
+BatchKernel batch_kernel(int cand) {
+    switch (cand) {
+        case 0: return k_step_batch<32, 4, ST>;
+        case 2: return k_step_batch<32, 16, ST>;
+        case 3: return k_step_batch<64, 2, ST>;
+        case 4: return k_step_batch<64, 4, ST>;
+        default: return k_step_batch<32, 8, ST>;
+    }
+}
+
+BatchKernel batch_kernel_for(int storage, int cand) {
+    if (storage == LBM_STORE_FP16_SHIFTED) return batch_kernel<ST_FP16>(cand);
+    if (storage == LBM_STORE_BF16_SHIFTED) return batch_kernel<ST_BF16>(cand);
+    return batch_kernel<ST_FP32>(cand);
+}
+
+}  // namespace
+
+struct lbm_batch {
+    int ncases = 0;
+    std::vector<lbm_handle*> cases;
+    int storage = 0;
+    int device = 0;
+    cudaStream_t user = nullptr;  // the cases' stream
+    cudaStream_t bs = nullptr;    // private stream (capturable)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
+    BatchTable* table = nullptr;  // one per tile height (host side; passed by value)
+    int cand = 1;                 // tile shape in use (index into BATCH_TX, BATCH_TY)
+    bool tuned = false;
+    double tuned_us[BATCH_NCAND] = {};
+    cudaGraphExec_t graph = nullptr;
+    long long node_count = 0;
+    char err[512] = {0};
+};
+
+static lbm_status bfail(lbm_batch* b, lbm_status st, const char* fmt, ...) {
+    if (b) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(b->err, sizeof b->err, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define LBM_BCUDA(b, call)                                                                  \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return bfail(b, LBM_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                         __FILE__, __LINE__);                                               \
+    } while (0)
+
+static void batch_release(lbm_batch* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    delete[] b->table;
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->t0) cudaEventDestroy(b->t0);
+    if (b->t1) cudaEventDestroy(b->t1);
+    if (b->bs) cudaStreamDestroy(b->bs);
+}
+
+// Take each case's current buffer from its handle (a case may have been
+// stepped on its own since the last batch step); a change invalidates the
+// captured graph, whose launches carry the table.
+static void batch_sync_table(lbm_batch* b) {
+    bool changed = false;
+    for (int c = 0; c < b->ncases; ++c)
+        for (int k = 0; k < BATCH_NCAND; ++k)
+            if (b->table[k].c[c].cur != b->cases[c]->cur) {
+                b->table[k].c[c].cur = b->cases[c]->cur;
+                changed = true;
+            }
+    if (changed && b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+}
+
+static lbm_status batch_launch(lbm_batch* b, int cand, int parity) {
+    BatchKernel k = batch_kernel_for(b->storage, cand);
+    const BatchTable& T = b->table[cand];
+    k<<<T.tile0[T.ncases], dim3(BATCH_TX[cand], BATCH_TY[cand]), 0, b->bs>>>(T, parity);
+    LBM_BCUDA(b, cudaGetLastError());
+    return LBM_OK;
+}
+
+// after an odd number of batch steps every case's current buffer flips
+static void batch_flip(lbm_batch* b, long long steps) {
+    if (steps & 1)
+        for (int c = 0; c < b->ncases; ++c) b->cases[c]->cur ^= 1;
+}
+
+extern "C" {
+
+lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** out) {
+    if (!out) return LBM_ERR_INVALID;
+    *out = nullptr;
+    if (ncases < 1 || ncases > BATCH_MAX_CASES || !cases) {
+        fprintf(stderr, "lbm_batch_create: need 1 <= ncases <= %d and a case array\n",
+                BATCH_MAX_CASES);
+        return LBM_ERR_INVALID;
+    }
+    for (int c = 0; c < ncases; ++c) {
+        const lbm_handle* h = cases[c];
+        if (!h || !h->inited || h->device != cases[0]->device || h->stream != cases[0]->stream ||
+            h->prm.storage != cases[0]->prm.storage) {
+            fprintf(stderr, "lbm_batch_create: case %d is NULL, not initialised, or differs in "
+                            "device, stream or storage from case 0\n", c);
+            return LBM_ERR_INVALID;
+        }
+        for (int d = 0; d < c; ++d)
+            if (cases[d] == h) {
+                fprintf(stderr, "lbm_batch_create: case %d repeats case %d\n", c, d);
+                return LBM_ERR_INVALID;
+            }
+    }
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_ERR_OOM;
+    b->ncases = ncases;
+    b->cases.assign(cases, cases + ncases);
+    b->storage = cases[0]->prm.storage;
+    b->device = cases[0]->device;
+    b->user = cases[0]->stream;
+    auto bad = [&](lbm_status st) {
+        fprintf(stderr, "lbm_batch_create: %s\n", b->err);
+        batch_release(b);
+        delete b;
+        return st;
+    };
+    if (cudaSetDevice(b->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->bs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&b->t0) != cudaSuccess || cudaEventCreate(&b->t1) != cudaSuccess) {
+        bfail(b, LBM_ERR_CUDA, "stream/event creation failed");
+        return bad(LBM_ERR_CUDA);
+    }
+    b->table = new (std::nothrow) BatchTable[BATCH_NCAND];
+    if (!b->table) {
+        bfail(b, LBM_ERR_OOM, "table allocation failed");
+        return bad(LBM_ERR_OOM);
+    }
+    for (int k = 0; k < BATCH_NCAND; ++k) {
+        BatchTable& T = b->table[k];
+        memset(&T, 0, sizeof T);
+        T.ncases = ncases;
+        long long tiles = 0;
+        for (int c = 0; c < ncases; ++c) {
+            lbm_handle* h = cases[c];
+            CaseDesc& d = T.c[c];
+            d.f[0] = h->f[0];
+            d.f[1] = h->f[1];
+            d.g[0] = h->g[0];
+            d.g[1] = h->g[1];
+            d.phiu = h->phiu;
+            d.flag = h->flag;
+            d.nx = h->nx;
+            d.ny = h->ny;
+            d.cur = h->cur;
+            d.m = h->model;
+            T.tiles_x[c] = (h->nx + BATCH_TX[k] - 1) / BATCH_TX[k];
+            T.tile0[c] = (int)tiles;
+            tiles += (long long)T.tiles_x[c] * ((h->ny + BATCH_TY[k] - 1) / BATCH_TY[k]);
+        }
+        if (tiles >= (1LL << 31) - 1) {
+            bfail(b, LBM_ERR_INVALID, "batch too large for one launch");
+            return bad(LBM_ERR_INVALID);
+        }
+        T.tile0[ncases] = (int)tiles;
+    }
+    for (int c = 0; c < ncases; ++c) b->node_count += (long long)cases[c]->N;
+    *out = b;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->bs);
+    batch_release(b);
+    delete b;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : "null batch"; }
+
+lbm_status lbm_batch_info(const lbm_batch* b, int* tile_tx, int* tile_ty, double* us_per_step,
+                          int* tuned) {
+    if (!b) return LBM_ERR_INVALID;
+    if (tile_tx) *tile_tx = BATCH_TX[b->cand];
+    if (tile_ty) *tile_ty = BATCH_TY[b->cand];
+    if (us_per_step) *us_per_step = b->tuned_us[b->cand];
+    if (tuned) *tuned = b->tuned ? 1 : 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
+    if (!b) return LBM_ERR_INVALID;
+    if (nsteps < 0) return bfail(b, LBM_ERR_INVALID, "lbm_batch_step: nsteps < 0");
+    if (nsteps == 0) return LBM_OK;
+    LBM_BCUDA(b, cudaSetDevice(b->device));
+    // order after earlier work on the cases' stream
+    LBM_BCUDA(b, cudaEventRecord(b->ev_in, b->user));
+    LBM_BCUDA(b, cudaStreamWaitEvent(b->bs, b->ev_in, 0));
+    batch_sync_table(b);
+    lbm_status st = LBM_OK;
+
+    long long done = 0;
+    // tune on the first call long enough: each candidate runs a few steps,
+    // timed, on the live state (all candidates give the same bits)
+    const int tune_steps = BATCH_NCAND * (BATCH_TUNE_WARM + BATCH_TUNE_STEPS);
+    if (!b->tuned && nsteps >= tune_steps) {
+        double best = 1e300;
+        for (int k = 0; k < BATCH_NCAND; ++k) {
+            for (int s = 0; s < BATCH_TUNE_WARM; ++s, ++done)
+                if ((st = batch_launch(b, k, (int)(done & 1))) != LBM_OK) return st;
+            LBM_BCUDA(b, cudaEventRecord(b->t0, b->bs));
+            for (int s = 0; s < BATCH_TUNE_STEPS; ++s, ++done)
+                if ((st = batch_launch(b, k, (int)(done & 1))) != LBM_OK) return st;
+            LBM_BCUDA(b, cudaEventRecord(b->t1, b->bs));
+            LBM_BCUDA(b, cudaEventSynchronize(b->t1));
+            float ms = 0.f;
+            LBM_BCUDA(b, cudaEventElapsedTime(&ms, b->t0, b->t1));
+            b->tuned_us[k] = 1e3 * ms / BATCH_TUNE_STEPS;
+            if (b->tuned_us[k] < best) {
+                best = b->tuned_us[k];
+                b->cand = k;
+            }
+        }
+        b->tuned = true;
+    }
+    // an odd count so far: run one more step so the graph starts at parity 0
+    if ((done & 1) && done < nsteps) {
+        if ((st = batch_launch(b, b->cand, 1)) != LBM_OK) return st;
+        ++done;
+    }
+    // whole graph replays (BATCH_GRAPH_STEPS steps each, parity returns to 0)
+    const long long reps = (nsteps - done) / BATCH_GRAPH_STEPS;
+    if (reps > 0) {
+        if (!b->graph) {
+            cudaGraph_t g;
+            LBM_BCUDA(b, cudaStreamBeginCapture(b->bs, cudaStreamCaptureModeThreadLocal));
+            for (int s = 0; s < BATCH_GRAPH_STEPS; ++s) {
+                BatchKernel k = batch_kernel_for(b->storage, b->cand);
+                const BatchTable& T = b->table[b->cand];
+                k<<<T.tile0[T.ncases], dim3(BATCH_TX[b->cand], BATCH_TY[b->cand]), 0, b->bs>>>(T, s & 1);
+            }
+            cudaError_t ce = cudaStreamEndCapture(b->bs, &g);
+            if (ce != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+        }
+        for (long long r = 0; r < reps; ++r) LBM_BCUDA(b, cudaGraphLaunch(b->graph, b->bs));
+        done += reps * BATCH_GRAPH_STEPS;
+    }
+    for (; done < nsteps; ++done)
+        if ((st = batch_launch(b, b->cand, (int)(done & 1))) != LBM_OK) return st;
+    // cases' current buffers (and with them the table) follow
+    batch_flip(b, nsteps);
+    batch_sync_table(b);
+    LBM_BCUDA(b, cudaEventRecord(b->ev_out, b->bs));
+    LBM_BCUDA(b, cudaStreamWaitEvent(b->user, b->ev_out, 0));
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -31,7 +31,8 @@ LBM_KERNEL_AUTO, LBM_KERNEL_GENERIC, LBM_KERNEL_TMA = 0, 1, 2
 # every entry point include/lbm_pf.h declares
 EXPORTS = ("lbm_create", "lbm_init", "lbm_step", "lbm_get_fields", "lbm_state_bytes",
            "lbm_get_state", "lbm_set_state", "lbm_diag", "lbm_synchronize", "lbm_destroy",
-           "lbm_last_error", "lbm_diag_fields_noalloc")
+           "lbm_last_error", "lbm_diag_fields_noalloc", "lbm_batch_create", "lbm_batch_step",
+           "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error")
 
 
 class LbmError(RuntimeError):
@@ -84,6 +85,16 @@ def load() -> ctypes.CDLL:
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_diag_fields_noalloc.argtypes = [vp, sz, vp, vp, ctypes.c_char_p, sz]
     L.lbm_diag_fields_noalloc.restype = ctypes.c_int
+    L.lbm_batch_create.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.lbm_batch_create.restype = ctypes.c_int
+    L.lbm_batch_step.argtypes = [vp, i]
+    L.lbm_batch_step.restype = ctypes.c_int
+    L.lbm_batch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), pd, ctypes.POINTER(i)]
+    L.lbm_batch_info.restype = ctypes.c_int
+    L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
+    L.lbm_batch_last_error.argtypes = [vp]
+    L.lbm_batch_last_error.restype = ctypes.c_char_p
     for name in ("lbm_create", "lbm_init", "lbm_step", "lbm_get_fields", "lbm_get_state",
                  "lbm_set_state", "lbm_diag", "lbm_synchronize"):
         getattr(L, name).restype = ctypes.c_int
@@ -200,6 +211,52 @@ class Lattice:
     def close(self):
         if getattr(self, "_h", None):
             self._L.lbm_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many Lattice cases stepped together (lbm_batch_*).  The lattices stay
+    owned by the caller and must outlive the batch."""
+
+    def __init__(self, lattices):
+        self._L = load()
+        self.lattices = list(lattices)
+        arr = (ctypes.c_void_p * len(self.lattices))(*(lat._h.value for lat in self.lattices))
+        h = ctypes.c_void_p()
+        rc = self._L.lbm_batch_create(len(self.lattices), arr, ctypes.byref(h))
+        if rc != LBM_OK:
+            raise LbmError(rc, "lbm_batch_create failed (see stderr)")
+        self._h = h
+
+    def step(self, nsteps: int = 1):
+        rc = self._L.lbm_batch_step(self._h, int(nsteps))
+        if rc != LBM_OK:
+            raise LbmError(rc, self._L.lbm_batch_last_error(self._h).decode())
+        return self
+
+    def info(self):
+        """((tile width, tile height), microseconds per step at tuning, tuned?)"""
+        tx, ty, tuned = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        us = ctypes.c_double()
+        self._L.lbm_batch_info(self._h, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(us),
+                               ctypes.byref(tuned))
+        return (tx.value, ty.value), us.value, bool(tuned.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lbm_batch_destroy(self._h)
             self._h = None
 
     def __enter__(self):

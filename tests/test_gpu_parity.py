@@ -263,7 +263,7 @@ def test_init_state_matches_oracle(lbm):
 
 # ---------------------------------------------------------------- tier 3 ----
 
-def test_static_drop_cfg1_horizon_and_integrals(lbm):
+def test_static_drop_64_horizon_and_integrals(lbm):
     """Static droplet 64 x 64, R = 16, ratio 1000, sigma = 0.01, tau = 0.8:
     pointwise within 1e-5 (p 3e-5) for 50 steps, then after 3000 steps the
     Laplace pressure jump, the spurious-velocity maximum and the density

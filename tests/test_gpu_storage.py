@@ -9,7 +9,7 @@ arithmetic stays FP32, only the stored populations are rounded.
   others; g_i stores S g_i / w_i and may differ by 2^-p of itself.
 * sum phi stays conserved (f_0 is the remainder of the node's phi).
 * A saved state restores bit for bit.
-* Accuracy on the static droplet (config 1) against the FP64 oracle: the
+* Accuracy on the 64 x 64 static droplet (R = 16, ratio 1000) against the FP64 oracle: the
   Laplace pressure jump and the spurious-velocity maximum, with the bounds
   this storage reaches."""
 import numpy as np
@@ -129,7 +129,7 @@ ACCURACY = {0: (0.03, 1.2), 1: (0.03, 1.5), 2: (0.30, 6.0)}   # storage -> (dp r
 
 @pytest.mark.parametrize("storage", [0, 1, 2])
 def test_static_drop_accuracy_per_storage(lbm, storage):
-    """Config 1 (64 x 64, R = 16, ratio 1000, sigma = 0.01): time-averaged
+    """Static drop (64 x 64, R = 16, ratio 1000, sigma = 0.01): time-averaged
     Laplace jump and spurious-velocity maximum against the FP64 oracle."""
     nx = ny = 64
     P = cases.params_static_drop()
