@@ -133,12 +133,21 @@ __device__ __forceinline__ void cdot9(float vx, float vy, float c[9]) {
     c[8] = -d;
 }
 
-// phi = sum_i f_i (Eq. 12), in one fixed association order everywhere so a
-// node's phi is bit-identical whichever block computes it.
-__device__ __forceinline__ float sum9(const float v[9]) {
-    return add(add(add(v[0], add(v[1], v[3])), add(v[2], v[4])),
-               add(add(v[5], v[7]), add(v[6], v[8])));
+// sum of the eight moving populations, in the association order used both
+// for phi below and for the rest population written as the remainder
+// phi - sum8 after the collision
+__device__ __forceinline__ float sum8(const float v[9]) {
+    return add(add(add(v[1], v[3]), add(v[2], v[4])), add(add(v[5], v[7]), add(v[6], v[8])));
 }
+
+// phi = sum_i f_i (Eq. 12), in one fixed association order everywhere so a
+// node's phi is bit-identical whichever block computes it.  The rest
+// population is added last, to the same tree of the moving ones that the
+// remainder subtracts: where the pulled moving populations equal the node's
+// own (uniform bulk), f_0 + sum8 then gives back phi exactly (f_0 = phi - sum8
+// is exact by Sterbenz's lemma when sum8 lies in [phi/2, 2 phi]), so the
+// rounding of the two sums cannot drift sum phi in one direction.
+__device__ __forceinline__ float sum9(const float v[9]) { return add(v[0], sum8(v)); }
 
 // coordinate of a tile/halo slot folded into the grid: periodic wrap in x;
 // in y wrap, or clamp at a wall (mirror ghost phi(-1) = phi(0)).

@@ -193,9 +193,7 @@ __global__ void k_init(const double* __restrict__ in, void* __restrict__ fd,
                 eq_at(in, N, n, j, m, fe, ge);
                 d[j] = Pop<ST>::round_f(j, fe);
             }
-            Pop<ST>::putf(fd, N32, 0, (int)n,
-                          sub(phi, add(add(add(d[1], d[3]), add(d[2], d[4])),
-                                       add(add(d[5], d[7]), add(d[6], d[8])))));
+            Pop<ST>::putf(fd, N32, 0, (int)n, sub(phi, sum8(d)));
         }
         phiu[n] = mul(phi, (float)in[N + n]);
         phiu[N + n] = mul(phi, (float)in[2 * N + n]);

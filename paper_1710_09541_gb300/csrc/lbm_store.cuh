@@ -43,8 +43,7 @@ struct Pop<ST_FP32> {
     __device__ static void stf(void* b, int N, int idx, const float f[9], float phi) {
 #pragma unroll
         for (int i = 1; i < 9; ++i) static_cast<float*>(b)[i * N + idx] = f[i];
-        static_cast<float*>(b)[idx] =
-            sub(phi, add(add(add(f[1], f[3]), add(f[2], f[4])), add(add(f[5], f[7]), add(f[6], f[8]))));
+        static_cast<float*>(b)[idx] = sub(phi, sum8(f));
     }
     __device__ static void stg(void* b, int N, int idx, const float g[9]) {
 #pragma unroll
@@ -55,7 +54,7 @@ struct Pop<ST_FP32> {
                                 const float g[9], float phi) {
         float* F = static_cast<float*>(fb);
         float* G = static_cast<float*>(gb);
-        F[idx] = sub(phi, add(add(add(f[1], f[3]), add(f[2], f[4])), add(add(f[5], f[7]), add(f[6], f[8]))));
+        F[idx] = sub(phi, sum8(f));
         G[idx] = g[0];
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
@@ -130,8 +129,7 @@ struct Shifted16 {
             fh(b, N)[(i - 1) * N + idx] = e;
             d[i] = dec_f(i, e);
         }
-        static_cast<float*>(b)[idx] =
-            sub(phi, add(add(add(d[1], d[3]), add(d[2], d[4])), add(add(d[5], d[7]), add(d[6], d[8]))));
+        static_cast<float*>(b)[idx] = sub(phi, sum8(d));
     }
     __device__ static void stg(void* b, int N, int idx, const float g[9]) {
 #pragma unroll
