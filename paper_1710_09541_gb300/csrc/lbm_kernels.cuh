@@ -85,12 +85,23 @@ __device__ __forceinline__ void pull9(const float* __restrict__ s, size_t Nz, co
     v[0] = __ldg(s + (q.r0 + q.x));
     v[1] = __ldg(s + (N + q.r0 + q.xm));
     v[3] = __ldg(s + (3 * N + q.r0 + q.xp));
-    v[2] = q.lo ? __ldg(s + (4 * N + q.r0 + q.x)) : __ldg(s + (2 * N + q.rm + q.x));
-    v[4] = q.hi ? __ldg(s + (2 * N + q.r0 + q.x)) : __ldg(s + (4 * N + q.rp + q.x));
-    v[5] = q.lo ? __ldg(s + (7 * N + q.r0 + q.x)) : __ldg(s + (5 * N + q.rm + q.xm));
-    v[6] = q.lo ? __ldg(s + (8 * N + q.r0 + q.x)) : __ldg(s + (6 * N + q.rm + q.xp));
-    v[7] = q.hi ? __ldg(s + (5 * N + q.r0 + q.x)) : __ldg(s + (7 * N + q.rp + q.xp));
-    v[8] = q.hi ? __ldg(s + (6 * N + q.r0 + q.x)) : __ldg(s + (8 * N + q.rp + q.xm));
+    // A wall row is uniform across a warp (a warp covers part of one tile
+    // row), so this is a branch, not a per-lane select of two loads.
+    if (q.lo || q.hi) {
+        v[2] = q.lo ? __ldg(s + (4 * N + q.r0 + q.x)) : __ldg(s + (2 * N + q.rm + q.x));
+        v[4] = q.hi ? __ldg(s + (2 * N + q.r0 + q.x)) : __ldg(s + (4 * N + q.rp + q.x));
+        v[5] = q.lo ? __ldg(s + (7 * N + q.r0 + q.x)) : __ldg(s + (5 * N + q.rm + q.xm));
+        v[6] = q.lo ? __ldg(s + (8 * N + q.r0 + q.x)) : __ldg(s + (6 * N + q.rm + q.xp));
+        v[7] = q.hi ? __ldg(s + (5 * N + q.r0 + q.x)) : __ldg(s + (7 * N + q.rp + q.xp));
+        v[8] = q.hi ? __ldg(s + (6 * N + q.r0 + q.x)) : __ldg(s + (8 * N + q.rp + q.xm));
+    } else {
+        v[2] = __ldg(s + (2 * N + q.rm + q.x));
+        v[4] = __ldg(s + (4 * N + q.rp + q.x));
+        v[5] = __ldg(s + (5 * N + q.rm + q.xm));
+        v[6] = __ldg(s + (6 * N + q.rm + q.xp));
+        v[7] = __ldg(s + (7 * N + q.rp + q.xp));
+        v[8] = __ldg(s + (8 * N + q.rp + q.xm));
+    }
 }
 
 // Explicitly rounded FP32 operations.  All arithmetic of the step goes

@@ -89,8 +89,8 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
             pull9(fs, N, q, f);
             pull9(gs, N, q, g);
         } else {
-            pull9f<ST>(fs, N32, q, f);
-            pull9g<ST>(gs, N32, q, g);
+            pull9f<ST, WALLS>(fs, N32, q, f);
+            pull9g<ST, WALLS>(gs, N32, q, g);
         }
         sphi[ty + 1][tx + 1] = sum9(f);
     } else {

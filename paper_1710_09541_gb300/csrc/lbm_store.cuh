@@ -121,6 +121,14 @@ struct Shifted16 {
     __device__ static float ldg(const void* b, int N, int i, int idx) {
         return dec_g(i, __ldg(static_cast<const unsigned short*>(b) + (i * N + idx)));
     }
+    // undecoded 16-bit words (f: i > 0), so a pull can issue all its loads
+    // before the first decode waits on one
+    __device__ static unsigned short rawf(const void* b, int N, int i, int idx) {
+        return __ldg(fh(b, N) + ((i - 1) * N + idx));
+    }
+    __device__ static unsigned short rawg(const void* b, int N, int i, int idx) {
+        return __ldg(static_cast<const unsigned short*>(b) + (i * N + idx));
+    }
     __device__ static void stf(void* b, int N, int idx, const float f[9], float phi) {
         float d[9];
 #pragma unroll
@@ -158,30 +166,65 @@ struct Pop<ST_FP16> : Shifted16<__half> {};
 template <>
 struct Pop<ST_BF16> : Shifted16<__nv_bfloat16> {};
 
-// Pull (stream) the 9 populations of node q through a storage format.
-template <int ST>
-__device__ __forceinline__ void pull9f(const void* s, int N, const Nbr& q, float v[9]) {
-    v[0] = Pop<ST>::ldf(s, N, 0, q.r0 + q.x);
-    v[1] = Pop<ST>::ldf(s, N, 1, q.r0 + q.xm);
-    v[3] = Pop<ST>::ldf(s, N, 3, q.r0 + q.xp);
-    v[2] = q.lo ? Pop<ST>::ldf(s, N, 4, q.r0 + q.x) : Pop<ST>::ldf(s, N, 2, q.rm + q.x);
-    v[4] = q.hi ? Pop<ST>::ldf(s, N, 2, q.r0 + q.x) : Pop<ST>::ldf(s, N, 4, q.rp + q.x);
-    v[5] = q.lo ? Pop<ST>::ldf(s, N, 7, q.r0 + q.x) : Pop<ST>::ldf(s, N, 5, q.rm + q.xm);
-    v[6] = q.lo ? Pop<ST>::ldf(s, N, 8, q.r0 + q.x) : Pop<ST>::ldf(s, N, 6, q.rm + q.xp);
-    v[7] = q.hi ? Pop<ST>::ldf(s, N, 5, q.r0 + q.x) : Pop<ST>::ldf(s, N, 7, q.rp + q.xp);
-    v[8] = q.hi ? Pop<ST>::ldf(s, N, 6, q.r0 + q.x) : Pop<ST>::ldf(s, N, 8, q.rp + q.xm);
+// Pull (stream) the 9 populations of node q through a 16-bit storage format:
+// all nine loads first, then the decodes.  The six wall-dependent loads sit
+// in a branch that is uniform across a warp when the wall flag is a run-time
+// value (BR, the batched kernel: fewer instructions), and are per-lane
+// selects when the kernel is compiled for walls (measured 5% faster there).
+template <int ST, bool F, bool BR>
+__device__ __forceinline__ void pull9_16(const void* s, int N, const Nbr& q, float v[9]) {
+    using P = Pop<ST>;
+    auto raw = [&](int i, int idx) { return F ? P::rawf(s, N, i, idx) : P::rawg(s, N, i, idx); };
+    unsigned short u[9];
+    float v0 = 0.f;
+    if (F)
+        v0 = __ldg(static_cast<const float*>(s) + (q.r0 + q.x));
+    else
+        u[0] = raw(0, q.r0 + q.x);
+    u[1] = raw(1, q.r0 + q.xm);
+    u[3] = raw(3, q.r0 + q.xp);
+    if (!BR || q.lo || q.hi) {
+        u[2] = q.lo ? raw(4, q.r0 + q.x) : raw(2, q.rm + q.x);
+        u[4] = q.hi ? raw(2, q.r0 + q.x) : raw(4, q.rp + q.x);
+        u[5] = q.lo ? raw(7, q.r0 + q.x) : raw(5, q.rm + q.xm);
+        u[6] = q.lo ? raw(8, q.r0 + q.x) : raw(6, q.rm + q.xp);
+        u[7] = q.hi ? raw(5, q.r0 + q.x) : raw(7, q.rp + q.xp);
+        u[8] = q.hi ? raw(6, q.r0 + q.x) : raw(8, q.rp + q.xm);
+    } else {
+        u[2] = raw(2, q.rm + q.x);
+        u[4] = raw(4, q.rp + q.x);
+        u[5] = raw(5, q.rm + q.xm);
+        u[6] = raw(6, q.rm + q.xp);
+        u[7] = raw(7, q.rp + q.xp);
+        u[8] = raw(8, q.rp + q.xm);
+    }
+    // a bounce-back link decodes with the stored direction's weight: opposite
+    // directions share w_i, so the stored and the pulled index agree on it
+    if (F) {
+        v[0] = v0;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) v[i] = P::dec_f(i, u[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v[i] = P::dec_g(i, u[i]);
+    }
 }
-template <int ST>
+
+// Pull the 9 populations of node q in any storage format (WALLS as in
+// make_nbr: < 0 when the wall flag is a run-time value).
+template <int ST, int WALLS = -1>
+__device__ __forceinline__ void pull9f(const void* s, int N, const Nbr& q, float v[9]) {
+    if constexpr (ST == ST_FP32)
+        pull9(static_cast<const float*>(s), (size_t)N, q, v);
+    else
+        pull9_16<ST, true, (WALLS < 0)>(s, N, q, v);
+}
+template <int ST, int WALLS = -1>
 __device__ __forceinline__ void pull9g(const void* s, int N, const Nbr& q, float v[9]) {
-    v[0] = Pop<ST>::ldg(s, N, 0, q.r0 + q.x);
-    v[1] = Pop<ST>::ldg(s, N, 1, q.r0 + q.xm);
-    v[3] = Pop<ST>::ldg(s, N, 3, q.r0 + q.xp);
-    v[2] = q.lo ? Pop<ST>::ldg(s, N, 4, q.r0 + q.x) : Pop<ST>::ldg(s, N, 2, q.rm + q.x);
-    v[4] = q.hi ? Pop<ST>::ldg(s, N, 2, q.r0 + q.x) : Pop<ST>::ldg(s, N, 4, q.rp + q.x);
-    v[5] = q.lo ? Pop<ST>::ldg(s, N, 7, q.r0 + q.x) : Pop<ST>::ldg(s, N, 5, q.rm + q.xm);
-    v[6] = q.lo ? Pop<ST>::ldg(s, N, 8, q.r0 + q.x) : Pop<ST>::ldg(s, N, 6, q.rm + q.xp);
-    v[7] = q.hi ? Pop<ST>::ldg(s, N, 5, q.r0 + q.x) : Pop<ST>::ldg(s, N, 7, q.rp + q.xp);
-    v[8] = q.hi ? Pop<ST>::ldg(s, N, 6, q.r0 + q.x) : Pop<ST>::ldg(s, N, 8, q.rp + q.xm);
+    if constexpr (ST == ST_FP32)
+        pull9(static_cast<const float*>(s), (size_t)N, q, v);
+    else
+        pull9_16<ST, false, (WALLS < 0)>(s, N, q, v);
 }
 
 template <int ST, int WALLS = -1>
@@ -191,7 +234,7 @@ __device__ __forceinline__ float phi_at_st(const void* fs, int N, int x, int y, 
     if constexpr (ST == ST_FP32)  // the plain float pull (its address arithmetic measured faster)
         pull9(static_cast<const float*>(fs), (size_t)N, make_nbr<WALLS>(x, y, nx, ny, walls), v);
     else
-        pull9f<ST>(fs, N, make_nbr<WALLS>(x, y, nx, ny, walls), v);
+        pull9f<ST, WALLS>(fs, N, make_nbr<WALLS>(x, y, nx, ny, walls), v);
     return sum9(v);
 }
 
