@@ -253,7 +253,7 @@ def run_batched(torch, lbm, stream, steps, storage=1):
     b = lbm.Batch(bat)
     b.step(100)                                   # tile-shape tuning + warm-up
     t_bat = _time_steps(torch, stream, lambda: b.step(steps))
-    shape, tuned_us, _ = b.info()
+    info = b.info()
     d_bat, u_bat = accuracy(bat)
     b.close()
     for lat in bat:
@@ -267,12 +267,14 @@ def run_batched(torch, lbm, stream, steps, storage=1):
         "cases": len(specs), "nodes": nodes, "steps_per_case": steps + 5,
         "storage": STORAGE_NAMES[storage], "value": v_bat, "unit": UNIT,
         "sequential_fp32": v_seq, "speedup_vs_sequential_fp32": v_bat / v_seq,
-        "tile": list(shape), "tuned_us_per_step": tuned_us, "bytes_per_lu": bpl,
+        "tile": {k: list(info[k]["tile"]) for k in ("periodic", "walls")},
+        "tuned_us_per_step": {k: info[k]["us"] for k in ("periodic", "walls")},
+        "bytes_per_lu": bpl,
         "roofline_frac": v_bat * 1e6 * bpl / 1e9 / peak,
         "sum_phi_rel_drift_max": {"batched": max(d_bat), "sequential_fp32": max(d_seq)},
         "drop_umax_max": {"batched": max(u_bat[k] for k in drops),
                           "sequential_fp32": max(u_seq[k] for k in drops)},
-        "launches_per_step": 1,
+        "launches_per_step": 2,
     }
 
 

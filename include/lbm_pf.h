@@ -198,21 +198,27 @@ lbm_status lbm_diag_fields_noalloc(const double* d_fields, size_t n, double* d_o
  *   cases and a private stream; handles must outlive the batch.
  *   Errors: LBM_ERR_INVALID, LBM_ERR_OOM, LBM_ERR_CUDA (then *out == NULL).
  * lbm_batch_step -- advance every case by nsteps time steps (the same update as
- *   lbm_step, Sec. II, bit for bit).  One kernel launch per step covers the
- *   tiles of all cases; steps run as replays of a CUDA graph of 32 steps.  The
- *   first call with nsteps >= 100 times five tile shapes (32x4, 32x8, 32x16,
- *   64x2, 64x4 nodes) on its own first 100 steps and keeps the fastest.
+ *   lbm_step, Sec. II, bit for bit).  The cases form two classes, periodic in y
+ *   and walled in y; each class has a kernel compiled for its boundary and its
+ *   own stream, and one launch per step covers the tiles of all its cases.  The
+ *   two classes share no data, so their launch chains run concurrently.  Steps
+ *   run as replays of a CUDA graph of 32 steps per class.  The first call with
+ *   nsteps >= 100 times five tile shapes (32x4, 32x8, 32x16, 64x2, 64x4 nodes)
+ *   for each class on its own first 100 steps and keeps the fastest.
  *   Ordered after earlier work on the cases' stream, and later work on that
  *   stream waits for it.  A case may also be stepped on its own between batch
  *   steps.
- * lbm_batch_info -- tile shape in use, its measured microseconds per step
- *   (0 before tuning) and whether tuning ran; any pointer may be NULL.
+ * lbm_batch_info -- for class cls (0: periodic cases, 1: walled cases): the
+ *   number of cases, the tile shape in use, its measured microseconds per
+ *   step (0 before tuning or for an empty class) and whether tuning ran; any
+ *   output pointer may be NULL.  Errors: LBM_ERR_INVALID (NULL batch, cls not
+ *   0 or 1).
  */
 typedef struct lbm_batch lbm_batch;
 lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** out);
 lbm_status lbm_batch_step(lbm_batch* b, int nsteps);
-lbm_status lbm_batch_info(const lbm_batch* b, int* tile_tx, int* tile_ty, double* us_per_step,
-                          int* tuned);
+lbm_status lbm_batch_info(const lbm_batch* b, int cls, int* ncases, int* tile_tx, int* tile_ty,
+                          double* us_per_step, int* tuned);
 void lbm_batch_destroy(lbm_batch* b);
 const char* lbm_batch_last_error(const lbm_batch* b);
 

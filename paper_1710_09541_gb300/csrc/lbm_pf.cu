@@ -910,15 +910,14 @@ struct BatchTable {
 static_assert(sizeof(BatchTable) <= 32000, "kernel parameters are limited to 32 KB");
 
 // resident threads per SM the batch kernels are compiled for (sets the
-// register budget), and whether one body serves both boundary kinds
+// register budget)
 #ifndef LBM_BATCH_THREADS
 #define LBM_BATCH_THREADS 1024
 #endif
-#ifndef LBM_BATCH_ONE_BODY
-#define LBM_BATCH_ONE_BODY 1
-#endif
 
-template <int TX, int TY, int ST>
+// One time step of every case of one boundary class (WALLS = 0: periodic in
+// y, 1: walls in y): block t runs tile t of the concatenated tile lists.
+template <int TX, int TY, int ST, int WALLS>
 __global__ void __launch_bounds__(TX* TY, LBM_BATCH_THREADS / (TX * TY))
     k_step_batch(const __grid_constant__ BatchTable T, int parity) {
     __shared__ float sphi[TY + 2][TX + 2];
@@ -933,20 +932,12 @@ __global__ void __launch_bounds__(TX* TY, LBM_BATCH_THREADS / (TX * TY))
     const int lt = t - T.tile0[lo];
     const int x0 = (lt % T.tiles_x[lo]) * TX, y0 = (lt / T.tiles_x[lo]) * TY;
     const int c = (cd.cur + parity) & 1;
-#if LBM_BATCH_ONE_BODY
-    step_tile<TX, TY, false, -1, ST>(sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu,
-                                     cd.flag, nullptr, cd.nx, cd.ny, cd.m, x0, y0);
-#else
-    // uniform per block: the periodic or the walled specialisation
-    if (cd.m.walls)
-        step_tile<TX, TY, false, 1, ST>(sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu,
+    step_tile<TX, TY, false, WALLS, ST>(sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu,
                                         cd.flag, nullptr, cd.nx, cd.ny, cd.m, x0, y0);
-    else
-        step_tile<TX, TY, false, 0, ST>(sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu,
-                                        cd.flag, nullptr, cd.nx, cd.ny, cd.m, x0, y0);
-#endif
 }
 
+// boundary classes: each has its own specialised kernel, stream and tile shape
+constexpr int BATCH_NCLASS = 2;  // 0: periodic cases, 1: walled cases
 // tile shapes the tuner times (TX x TY nodes, one thread each)
 constexpr int BATCH_NCAND = 5;
 constexpr int BATCH_TX[BATCH_NCAND] = {32, 32, 32, 64, 64};
@@ -956,21 +947,26 @@ constexpr int BATCH_TUNE_WARM = 4, BATCH_TUNE_STEPS = 16;
 
 using BatchKernel = void (*)(BatchTable, int);
 
-template <int ST>
+template <int ST, int W>
 BatchKernel batch_kernel(int cand) {
     switch (cand) {
-        case 0: return k_step_batch<32, 4, ST>;
-        case 2: return k_step_batch<32, 16, ST>;
-        case 3: return k_step_batch<64, 2, ST>;
-        case 4: return k_step_batch<64, 4, ST>;
-        default: return k_step_batch<32, 8, ST>;
+        case 0: return k_step_batch<32, 4, ST, W>;
+        case 2: return k_step_batch<32, 16, ST, W>;
+        case 3: return k_step_batch<64, 2, ST, W>;
+        case 4: return k_step_batch<64, 4, ST, W>;
+        default: return k_step_batch<32, 8, ST, W>;
     }
 }
 
-BatchKernel batch_kernel_for(int storage, int cand) {
-    if (storage == LBM_STORE_FP16_SHIFTED) return batch_kernel<ST_FP16>(cand);
-    if (storage == LBM_STORE_BF16_SHIFTED) return batch_kernel<ST_BF16>(cand);
-    return batch_kernel<ST_FP32>(cand);
+template <int ST>
+BatchKernel batch_kernel_st(int cls, int cand) {
+    return cls ? batch_kernel<ST, 1>(cand) : batch_kernel<ST, 0>(cand);
+}
+
+BatchKernel batch_kernel_for(int storage, int cls, int cand) {
+    if (storage == LBM_STORE_FP16_SHIFTED) return batch_kernel_st<ST_FP16>(cls, cand);
+    if (storage == LBM_STORE_BF16_SHIFTED) return batch_kernel_st<ST_BF16>(cls, cand);
+    return batch_kernel_st<ST_FP32>(cls, cand);
 }
 
 }  // namespace
@@ -978,18 +974,22 @@ BatchKernel batch_kernel_for(int storage, int cand) {
 struct lbm_batch {
     int ncases = 0;
     std::vector<lbm_handle*> cases;
+    std::vector<int> cls_of, slot_of;  // each case's class and its slot in the class table
+    int ncls[BATCH_NCLASS] = {0, 0};
     int storage = 0;
     int device = 0;
-    cudaStream_t user = nullptr;  // the cases' stream
-    cudaStream_t bs = nullptr;    // private stream (capturable)
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
-    BatchTable* table = nullptr;  // one per tile height (host side; passed by value)
-    int cand = 1;                 // tile shape in use (index into BATCH_TX, BATCH_TY)
+    cudaStream_t user = nullptr;                 // the cases' stream
+    cudaStream_t bs[BATCH_NCLASS] = {};          // private streams, one per class (capturable)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    BatchTable* table = nullptr;  // [class][shape], host side, passed by value
+    int cand[BATCH_NCLASS] = {1, 1};  // tile shape in use per class (index into BATCH_TX/TY)
     bool tuned = false;
-    double tuned_us[BATCH_NCAND] = {};
+    double tuned_us[BATCH_NCLASS][BATCH_NCAND] = {};
     cudaGraphExec_t graph = nullptr;
     long long node_count = 0;
     char err[512] = {0};
+    BatchTable& tab(int cls, int k) { return table[cls * BATCH_NCAND + k]; }
 };
 
 static lbm_status bfail(lbm_batch* b, lbm_status st, const char* fmt, ...) {
@@ -1013,35 +1013,59 @@ static lbm_status bfail(lbm_batch* b, lbm_status st, const char* fmt, ...) {
 static void batch_release(lbm_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     delete[] b->table;
-    if (b->ev_in) cudaEventDestroy(b->ev_in);
-    if (b->ev_out) cudaEventDestroy(b->ev_out);
-    if (b->t0) cudaEventDestroy(b->t0);
-    if (b->t1) cudaEventDestroy(b->t1);
-    if (b->bs) cudaStreamDestroy(b->bs);
+    for (cudaEvent_t e : {b->ev_in, b->ev_out, b->ev_fork, b->ev_join, b->t0, b->t1})
+        if (e) cudaEventDestroy(e);
+    for (int k = 0; k < BATCH_NCLASS; ++k)
+        if (b->bs[k]) cudaStreamDestroy(b->bs[k]);
 }
 
 // Take each case's current buffer from its handle (a case may have been
 // stepped on its own since the last batch step); a change invalidates the
-// captured graph, whose launches carry the table.
+// captured graph, whose launches carry the tables.
 static void batch_sync_table(lbm_batch* b) {
     bool changed = false;
     for (int c = 0; c < b->ncases; ++c)
-        for (int k = 0; k < BATCH_NCAND; ++k)
-            if (b->table[k].c[c].cur != b->cases[c]->cur) {
-                b->table[k].c[c].cur = b->cases[c]->cur;
+        for (int k = 0; k < BATCH_NCAND; ++k) {
+            CaseDesc& d = b->tab(b->cls_of[c], k).c[b->slot_of[c]];
+            if (d.cur != b->cases[c]->cur) {
+                d.cur = b->cases[c]->cur;
                 changed = true;
             }
+        }
     if (changed && b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
 }
 
-static lbm_status batch_launch(lbm_batch* b, int cand, int parity) {
-    BatchKernel k = batch_kernel_for(b->storage, cand);
-    const BatchTable& T = b->table[cand];
-    k<<<T.tile0[T.ncases], dim3(BATCH_TX[cand], BATCH_TY[cand]), 0, b->bs>>>(T, parity);
+// one step of class cls with tile shape cand, on the class's stream
+static lbm_status batch_launch(lbm_batch* b, int cls, int cand, int parity) {
+    BatchKernel k = batch_kernel_for(b->storage, cls, cand);
+    const BatchTable& T = b->tab(cls, cand);
+    k<<<T.tile0[T.ncases], dim3(BATCH_TX[cand], BATCH_TY[cand]), 0, b->bs[cls]>>>(T, parity);
     LBM_BCUDA(b, cudaGetLastError());
+    return LBM_OK;
+}
+
+// steps [from, to) of every non-empty class, each class on its own stream
+static lbm_status batch_run(lbm_batch* b, long long from, long long to) {
+    lbm_status st;
+    for (int cls = 0; cls < BATCH_NCLASS; ++cls)
+        if (b->ncls[cls])
+            for (long long s = from; s < to; ++s)
+                if ((st = batch_launch(b, cls, b->cand[cls], (int)(s & 1))) != LBM_OK) return st;
+    return LBM_OK;
+}
+
+// the class streams start after, and end before, the work on bs[0]
+static lbm_status batch_fork(lbm_batch* b) {
+    LBM_BCUDA(b, cudaEventRecord(b->ev_fork, b->bs[0]));
+    LBM_BCUDA(b, cudaStreamWaitEvent(b->bs[1], b->ev_fork, 0));
+    return LBM_OK;
+}
+static lbm_status batch_join(lbm_batch* b) {
+    LBM_BCUDA(b, cudaEventRecord(b->ev_join, b->bs[1]));
+    LBM_BCUDA(b, cudaStreamWaitEvent(b->bs[0], b->ev_join, 0));
     return LBM_OK;
 }
 
@@ -1049,6 +1073,60 @@ static lbm_status batch_launch(lbm_batch* b, int cand, int parity) {
 static void batch_flip(lbm_batch* b, long long steps) {
     if (steps & 1)
         for (int c = 0; c < b->ncases; ++c) b->cases[c]->cur ^= 1;
+}
+
+// Time every tile shape of each class on the live state (all shapes give the
+// same bits) and keep the fastest; the classes are timed one after the other.
+static lbm_status batch_tune(lbm_batch* b, long long& done) {
+    lbm_status st;
+    const long long start = done;
+    for (int cls = 0; cls < BATCH_NCLASS; ++cls) {
+        if (!b->ncls[cls]) continue;
+        long long s = start;
+        double best = 1e300;
+        for (int k = 0; k < BATCH_NCAND; ++k) {
+            for (int w = 0; w < BATCH_TUNE_WARM; ++w, ++s)
+                if ((st = batch_launch(b, cls, k, (int)(s & 1))) != LBM_OK) return st;
+            LBM_BCUDA(b, cudaEventRecord(b->t0, b->bs[cls]));
+            for (int w = 0; w < BATCH_TUNE_STEPS; ++w, ++s)
+                if ((st = batch_launch(b, cls, k, (int)(s & 1))) != LBM_OK) return st;
+            LBM_BCUDA(b, cudaEventRecord(b->t1, b->bs[cls]));
+            LBM_BCUDA(b, cudaEventSynchronize(b->t1));
+            float ms = 0.f;
+            LBM_BCUDA(b, cudaEventElapsedTime(&ms, b->t0, b->t1));
+            b->tuned_us[cls][k] = 1e3 * ms / BATCH_TUNE_STEPS;
+            if (b->tuned_us[cls][k] < best) {
+                best = b->tuned_us[cls][k];
+                b->cand[cls] = k;
+            }
+        }
+        done = s;
+    }
+    b->tuned = true;
+    return LBM_OK;
+}
+
+// Capture BATCH_GRAPH_STEPS steps (parities 0, 1, ...) of both classes, each
+// class a chain of launches on its own stream, the two chains independent.
+static lbm_status batch_capture(lbm_batch* b) {
+    cudaGraph_t g;
+    LBM_BCUDA(b, cudaStreamBeginCapture(b->bs[0], cudaStreamCaptureModeThreadLocal));
+    lbm_status st = batch_fork(b);
+    if (st == LBM_OK) st = batch_run(b, 0, BATCH_GRAPH_STEPS);
+    if (st == LBM_OK) st = batch_join(b);
+    cudaError_t ce = cudaStreamEndCapture(b->bs[0], &g);
+    if (st != LBM_OK) {
+        if (ce == cudaSuccess) cudaGraphDestroy(g);
+        return st;
+    }
+    if (ce != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+        b->graph = nullptr;
+        return bfail(b, LBM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    }
+    return LBM_OK;
 }
 
 extern "C" {
@@ -1079,6 +1157,13 @@ lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** ou
     if (!b) return LBM_ERR_OOM;
     b->ncases = ncases;
     b->cases.assign(cases, cases + ncases);
+    b->cls_of.resize(ncases);
+    b->slot_of.resize(ncases);
+    for (int c = 0; c < ncases; ++c) {
+        const int cls = cases[c]->model.walls ? 1 : 0;
+        b->cls_of[c] = cls;
+        b->slot_of[c] = b->ncls[cls]++;
+    }
     b->storage = cases[0]->prm.storage;
     b->device = cases[0]->device;
     b->user = cases[0]->stream;
@@ -1089,46 +1174,52 @@ lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** ou
         return st;
     };
     if (cudaSetDevice(b->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->bs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->bs[0], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->bs[1], cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&b->t0) != cudaSuccess || cudaEventCreate(&b->t1) != cudaSuccess) {
         bfail(b, LBM_ERR_CUDA, "stream/event creation failed");
         return bad(LBM_ERR_CUDA);
     }
-    b->table = new (std::nothrow) BatchTable[BATCH_NCAND];
+    b->table = new (std::nothrow) BatchTable[BATCH_NCLASS * BATCH_NCAND];
     if (!b->table) {
         bfail(b, LBM_ERR_OOM, "table allocation failed");
         return bad(LBM_ERR_OOM);
     }
-    for (int k = 0; k < BATCH_NCAND; ++k) {
-        BatchTable& T = b->table[k];
-        memset(&T, 0, sizeof T);
-        T.ncases = ncases;
-        long long tiles = 0;
-        for (int c = 0; c < ncases; ++c) {
-            lbm_handle* h = cases[c];
-            CaseDesc& d = T.c[c];
-            d.f[0] = h->f[0];
-            d.f[1] = h->f[1];
-            d.g[0] = h->g[0];
-            d.g[1] = h->g[1];
-            d.phiu = h->phiu;
-            d.flag = h->flag;
-            d.nx = h->nx;
-            d.ny = h->ny;
-            d.cur = h->cur;
-            d.m = h->model;
-            T.tiles_x[c] = (h->nx + BATCH_TX[k] - 1) / BATCH_TX[k];
-            T.tile0[c] = (int)tiles;
-            tiles += (long long)T.tiles_x[c] * ((h->ny + BATCH_TY[k] - 1) / BATCH_TY[k]);
+    for (int cls = 0; cls < BATCH_NCLASS; ++cls)
+        for (int k = 0; k < BATCH_NCAND; ++k) {
+            BatchTable& T = b->tab(cls, k);
+            memset(&T, 0, sizeof T);
+            T.ncases = b->ncls[cls];
+            long long tiles = 0;
+            for (int c = 0; c < ncases; ++c) {
+                if (b->cls_of[c] != cls) continue;
+                const lbm_handle* h = cases[c];
+                const int j = b->slot_of[c];
+                CaseDesc& d = T.c[j];
+                d.f[0] = h->f[0];
+                d.f[1] = h->f[1];
+                d.g[0] = h->g[0];
+                d.g[1] = h->g[1];
+                d.phiu = h->phiu;
+                d.flag = h->flag;
+                d.nx = h->nx;
+                d.ny = h->ny;
+                d.cur = h->cur;
+                d.m = h->model;
+                T.tiles_x[j] = (h->nx + BATCH_TX[k] - 1) / BATCH_TX[k];
+                T.tile0[j] = (int)tiles;
+                tiles += (long long)T.tiles_x[j] * ((h->ny + BATCH_TY[k] - 1) / BATCH_TY[k]);
+            }
+            if (tiles >= (1LL << 31) - 1) {
+                bfail(b, LBM_ERR_INVALID, "batch too large for one launch");
+                return bad(LBM_ERR_INVALID);
+            }
+            T.tile0[T.ncases] = (int)tiles;
         }
-        if (tiles >= (1LL << 31) - 1) {
-            bfail(b, LBM_ERR_INVALID, "batch too large for one launch");
-            return bad(LBM_ERR_INVALID);
-        }
-        T.tile0[ncases] = (int)tiles;
-    }
     for (int c = 0; c < ncases; ++c) b->node_count += (long long)cases[c]->N;
     *out = b;
     return LBM_OK;
@@ -1137,19 +1228,20 @@ lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** ou
 void lbm_batch_destroy(lbm_batch* b) {
     if (!b) return;
     cudaSetDevice(b->device);
-    cudaStreamSynchronize(b->bs);
+    for (int k = 0; k < BATCH_NCLASS; ++k) cudaStreamSynchronize(b->bs[k]);
     batch_release(b);
     delete b;
 }
 
 const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : "null batch"; }
 
-lbm_status lbm_batch_info(const lbm_batch* b, int* tile_tx, int* tile_ty, double* us_per_step,
-                          int* tuned) {
-    if (!b) return LBM_ERR_INVALID;
-    if (tile_tx) *tile_tx = BATCH_TX[b->cand];
-    if (tile_ty) *tile_ty = BATCH_TY[b->cand];
-    if (us_per_step) *us_per_step = b->tuned_us[b->cand];
+lbm_status lbm_batch_info(const lbm_batch* b, int cls, int* ncases, int* tile_tx, int* tile_ty,
+                          double* us_per_step, int* tuned) {
+    if (!b || cls < 0 || cls >= BATCH_NCLASS) return LBM_ERR_INVALID;
+    if (ncases) *ncases = b->ncls[cls];
+    if (tile_tx) *tile_tx = BATCH_TX[b->cand[cls]];
+    if (tile_ty) *tile_ty = BATCH_TY[b->cand[cls]];
+    if (us_per_step) *us_per_step = b->tuned_us[cls][b->cand[cls]];
     if (tuned) *tuned = b->tuned ? 1 : 0;
     return LBM_OK;
 }
@@ -1161,65 +1253,38 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
     LBM_BCUDA(b, cudaSetDevice(b->device));
     // order after earlier work on the cases' stream
     LBM_BCUDA(b, cudaEventRecord(b->ev_in, b->user));
-    LBM_BCUDA(b, cudaStreamWaitEvent(b->bs, b->ev_in, 0));
+    LBM_BCUDA(b, cudaStreamWaitEvent(b->bs[0], b->ev_in, 0));
     batch_sync_table(b);
-    lbm_status st = LBM_OK;
+    lbm_status st;
+    if ((st = batch_fork(b)) != LBM_OK) return st;
 
     long long done = 0;
-    // tune on the first call long enough: each candidate runs a few steps,
-    // timed, on the live state (all candidates give the same bits)
+    // tune on the first call long enough: it runs tune_steps real steps
     const int tune_steps = BATCH_NCAND * (BATCH_TUNE_WARM + BATCH_TUNE_STEPS);
-    if (!b->tuned && nsteps >= tune_steps) {
-        double best = 1e300;
-        for (int k = 0; k < BATCH_NCAND; ++k) {
-            for (int s = 0; s < BATCH_TUNE_WARM; ++s, ++done)
-                if ((st = batch_launch(b, k, (int)(done & 1))) != LBM_OK) return st;
-            LBM_BCUDA(b, cudaEventRecord(b->t0, b->bs));
-            for (int s = 0; s < BATCH_TUNE_STEPS; ++s, ++done)
-                if ((st = batch_launch(b, k, (int)(done & 1))) != LBM_OK) return st;
-            LBM_BCUDA(b, cudaEventRecord(b->t1, b->bs));
-            LBM_BCUDA(b, cudaEventSynchronize(b->t1));
-            float ms = 0.f;
-            LBM_BCUDA(b, cudaEventElapsedTime(&ms, b->t0, b->t1));
-            b->tuned_us[k] = 1e3 * ms / BATCH_TUNE_STEPS;
-            if (b->tuned_us[k] < best) {
-                best = b->tuned_us[k];
-                b->cand = k;
-            }
-        }
-        b->tuned = true;
-    }
-    // an odd count so far: run one more step so the graph starts at parity 0
+    if (!b->tuned && nsteps >= tune_steps)
+        if ((st = batch_tune(b, done)) != LBM_OK) return st;
+    // an odd count so far: one more step so the graph starts at parity 0
     if ((done & 1) && done < nsteps) {
-        if ((st = batch_launch(b, b->cand, 1)) != LBM_OK) return st;
+        if ((st = batch_run(b, done, done + 1)) != LBM_OK) return st;
         ++done;
     }
+    if ((st = batch_join(b)) != LBM_OK) return st;
     // whole graph replays (BATCH_GRAPH_STEPS steps each, parity returns to 0)
     const long long reps = (nsteps - done) / BATCH_GRAPH_STEPS;
     if (reps > 0) {
-        if (!b->graph) {
-            cudaGraph_t g;
-            LBM_BCUDA(b, cudaStreamBeginCapture(b->bs, cudaStreamCaptureModeThreadLocal));
-            for (int s = 0; s < BATCH_GRAPH_STEPS; ++s) {
-                BatchKernel k = batch_kernel_for(b->storage, b->cand);
-                const BatchTable& T = b->table[b->cand];
-                k<<<T.tile0[T.ncases], dim3(BATCH_TX[b->cand], BATCH_TY[b->cand]), 0, b->bs>>>(T, s & 1);
-            }
-            cudaError_t ce = cudaStreamEndCapture(b->bs, &g);
-            if (ce != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
-            ce = cudaGraphInstantiate(&b->graph, g, 0);
-            cudaGraphDestroy(g);
-            if (ce != cudaSuccess) return bfail(b, LBM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
-        }
-        for (long long r = 0; r < reps; ++r) LBM_BCUDA(b, cudaGraphLaunch(b->graph, b->bs));
-        done += reps * BATCH_GRAPH_STEPS;
+        if (!b->graph && (st = batch_capture(b)) != LBM_OK) return st;
+        for (long long r = 0; r < reps; ++r) LBM_BCUDA(b, cudaGraphLaunch(b->graph, b->bs[0]));
     }
-    for (; done < nsteps; ++done)
-        if ((st = batch_launch(b, b->cand, (int)(done & 1))) != LBM_OK) return st;
-    // cases' current buffers (and with them the table) follow
+    // the remainder, with parities continuing from 0 after the replays
+    if (done + reps * BATCH_GRAPH_STEPS < nsteps) {
+        if ((st = batch_fork(b)) != LBM_OK) return st;
+        if ((st = batch_run(b, done + reps * BATCH_GRAPH_STEPS, nsteps)) != LBM_OK) return st;
+        if ((st = batch_join(b)) != LBM_OK) return st;
+    }
+    // cases' current buffers (and with them the tables) follow
     batch_flip(b, nsteps);
     batch_sync_table(b);
-    LBM_BCUDA(b, cudaEventRecord(b->ev_out, b->bs));
+    LBM_BCUDA(b, cudaEventRecord(b->ev_out, b->bs[0]));
     LBM_BCUDA(b, cudaStreamWaitEvent(b->user, b->ev_out, 0));
     return LBM_OK;
 }

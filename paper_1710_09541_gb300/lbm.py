@@ -89,7 +89,8 @@ def load() -> ctypes.CDLL:
     L.lbm_batch_create.restype = ctypes.c_int
     L.lbm_batch_step.argtypes = [vp, i]
     L.lbm_batch_step.restype = ctypes.c_int
-    L.lbm_batch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), pd, ctypes.POINTER(i)]
+    L.lbm_batch_info.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), pd,
+                                  ctypes.POINTER(i)]
     L.lbm_batch_info.restype = ctypes.c_int
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
@@ -247,12 +248,20 @@ class Batch:
         return self
 
     def info(self):
-        """((tile width, tile height), microseconds per step at tuning, tuned?)"""
-        tx, ty, tuned = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        us = ctypes.c_double()
-        self._L.lbm_batch_info(self._h, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(us),
-                               ctypes.byref(tuned))
-        return (tx.value, ty.value), us.value, bool(tuned.value)
+        """{"periodic": {...}, "walls": {...}, "tuned": bool}; per class the
+        number of cases, the tile shape (width, height) in use and its
+        microseconds per step at tuning."""
+        out = {}
+        for cls, name in ((0, "periodic"), (1, "walls")):
+            n, tx, ty, tuned = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            us = ctypes.c_double()
+            rc = self._L.lbm_batch_info(self._h, cls, ctypes.byref(n), ctypes.byref(tx),
+                                        ctypes.byref(ty), ctypes.byref(us), ctypes.byref(tuned))
+            if rc != LBM_OK:
+                raise LbmError(rc, "lbm_batch_info failed")
+            out[name] = {"cases": n.value, "tile": (tx.value, ty.value), "us": us.value}
+            out["tuned"] = bool(tuned.value)
+        return out
 
     def close(self):
         if getattr(self, "_h", None):

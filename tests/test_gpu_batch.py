@@ -46,10 +46,38 @@ def test_batch_equals_individual_steps(lbm, storage):
             bt.step(7)
             A[2].step(3)
             bt.step(150)
-            shape, us, tuned = bt.info()
-            assert tuned and shape in ((32, 4), (32, 8), (32, 16), (64, 2), (64, 4)) and us > 0
+            info = bt.info()
+            assert info["tuned"]
+            assert info["periodic"]["cases"] == 3 and info["walls"]["cases"] == 3
+            for cls in ("periodic", "walls"):
+                assert info[cls]["tile"] in ((32, 4), (32, 8), (32, 16), (64, 2), (64, 4))
+                assert info[cls]["us"] > 0
         for k, lat in enumerate(B):
             lat.step(157 + (3 if k == 2 else 0))
+        for a, b in zip(A, B):
+            for x, y in zip(a.get_state(), b.get_state()):
+                assert np.array_equal(x, y)
+    finally:
+        for lat in A + B:
+            lat.close()
+
+
+@pytest.mark.parametrize("kinds", ["static_drop", "impact"])
+def test_batch_of_one_class(lbm, kinds):
+    """All cases in one boundary class (the other class empty), an odd step
+    count so the graph is re-captured on the next call."""
+    specs = [sp for sp in cases.batch_cases(n=8, seed=5) if sp["kind"] == kinds][:3]
+    A = _lattices(lbm, specs, 1)
+    B = _lattices(lbm, specs, 1)
+    try:
+        with lbm.Batch(A) as bt:
+            bt.step(101)
+            bt.step(65)
+            info = bt.info()
+            empty = "walls" if kinds == "static_drop" else "periodic"
+            assert info[empty]["cases"] == 0 and info[empty]["us"] == 0
+        for lat in B:
+            lat.step(166)
         for a, b in zip(A, B):
             for x, y in zip(a.get_state(), b.get_state()):
                 assert np.array_equal(x, y)
