@@ -33,6 +33,11 @@
  *     so single- and double-precision evaluations take the same branch.
  *   - At a half-way bounce-back wall the phi stencil uses a mirror ghost
  *     phi(y=-1) = phi(0), phi(ny) = phi(ny-1) (neutral wall).
+ *   - The "open" top boundary of the impact case (Sec. III D names it without
+ *     a rule) is a zero-gradient outflow: populations leaving through the top
+ *     are lost, the unknown incoming ones of the top row (c_y = -1) equal the
+ *     row below's after streaming, and the phi stencil's ghost row equals the
+ *     top row.  The initial state obeys the same rule.
  *   - The step-function viscosity of Eq. 26 takes the liquid value at
  *     phi >= 0.5 and converts to kinematic viscosity with nu = mu/rho(phi).
  *   - Initial populations are the equilibria of Eqs. 9 and 16.
@@ -67,7 +72,8 @@ typedef struct {
     double sigma, W;       /* Eq. 7 */
     double tau_h;          /* Allen-Cahn relaxation time (tau_f of Eq. 8) */
     double Gx, Gy;         /* body force density G, Eq. 4b / 19 */
-    int bc_y;              /* 0: periodic in y, 1: half-way bounce-back walls */
+    int bc_y;              /* 0: periodic in y, 1: half-way bounce-back walls,
+                              2: bounce-back wall at y = 0, open top */
     int normal_scheme;     /* 0: central gradient (Eq. 27), 1: local (Eq. 29) */
 } orc_params;
 
@@ -151,7 +157,8 @@ double orc_viscosity(const orc_params* P, double phi) {
 /* ---- finite differences, Eqs. 27 and 28 --------------------------------- */
 
 /* phi at (x, y) with periodic wrap in x and, in y, either wrap (bc_y = 0) or
- * the mirror ghost of a neutral wall (bc_y = 1). */
+ * the ghost row equal to the edge row (a neutral wall, or zero gradient at an
+ * open boundary). */
 static double phi_at(const double* phi, int nx, int ny, int bc_y, int x, int y) {
     x = ((x % nx) + nx) % nx;
     if (bc_y == 0) {
@@ -185,11 +192,28 @@ void orc_grad_lap(int nx, int ny, int bc_y, const double* phi,
         }
 }
 
+/* Open top (bc_y = 2): the populations that would enter the top row from
+ * outside (c_y = -1) take the values the row below holds for the same
+ * direction after streaming (zero normal gradient). */
+static void open_top_fill(double* f, double* g, int nx, int ny) {
+    const size_t N = (size_t)nx * ny;
+    for (int i = 0; i < 9; ++i) {
+        if (CY[i] != -1) continue;
+        for (int x = 0; x < nx; ++x) {
+            size_t top = (size_t)(ny - 1) * nx + x, below = (size_t)(ny - 2) * nx + x;
+            f[i * N + top] = f[i * N + below];
+            g[i * N + top] = g[i * N + below];
+        }
+    }
+}
+
 /* ---- lattice object ------------------------------------------------------ */
 
 int orc_create(int nx, int ny, const orc_params* p, orc_lattice** out) {
     if (nx < 1 || ny < 1 || !p || !out) return -1;
     if (p->normal_scheme != 0 && p->normal_scheme != 1) return -1;
+    if (p->bc_y < 0 || p->bc_y > 2) return -1;
+    if (p->bc_y == 2 && ny < 2) return -1; /* the open top copies the row below */
     orc_lattice* L = (orc_lattice*)calloc(1, sizeof(orc_lattice));
     if (!L) return -5;
     size_t N = (size_t)nx * ny;
@@ -246,6 +270,7 @@ int orc_init(orc_lattice* L, const double* phi0, const double* ux0,
         L->phiu_x[n] = phi * ux;
         L->phiu_y[n] = phi * uy;
     }
+    if (P->bc_y == 2) open_top_fill(L->f, L->g, L->nx, L->ny);
     return 0;
 }
 
@@ -384,6 +409,8 @@ static void one_step(orc_lattice* L) {
                 int id = i;
                 if (P->bc_y == 0) {
                     yd = ((yd % ny) + ny) % ny;
+                } else if (P->bc_y == 2 && yd > ny - 1) {
+                    continue; /* leaves through the open top */
                 } else if (yd < 0 || yd > ny - 1) {
                     xd = x;
                     yd = y;
@@ -397,6 +424,7 @@ static void one_step(orc_lattice* L) {
             L->phiu_y[n] = phi * uy;
         }
     }
+    if (P->bc_y == 2) open_top_fill(L->fs, L->gs, nx, ny);
     double* t;
     t = L->f; L->f = L->fs; L->fs = t;
     t = L->g; L->g = L->gs; L->gs = t;

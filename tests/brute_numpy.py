@@ -57,6 +57,14 @@ def nu_of(phi, p):
     return phi * (p["nu_l"] - p["nu_g"]) + p["nu_g"]
 
 
+def _open_top(f, g):
+    """Open top (bc_y = 2): the top row's incoming populations (c_y = -1)
+    repeat the row below's (zero normal gradient)."""
+    down = np.where(CY == -1)[0]
+    f[down, -1, :] = f[down, -2, :]
+    g[down, -1, :] = g[down, -2, :]
+
+
 def init(phi0, ux0, uy0, p0, p):
     rho = phi0 * (p["rho_l"] - p["rho_g"]) + p["rho_g"]
     cu = CX[:, None, None] * ux0 + CY[:, None, None] * uy0
@@ -65,11 +73,13 @@ def init(phi0, ux0, uy0, p0, p):
     s = W[:, None, None] * (3 * cu + 4.5 * cu ** 2 - 1.5 * usq)
     g = 3 * p0 * W[:, None, None] + rho * s
     g[0] -= 3 * p0
+    if p.get("bc_y", 0) == 2:
+        _open_top(f, g)
     return f, g, np.stack([phi0 * ux0, phi0 * uy0])
 
 
 def step(f, g, phiu, p):
-    walls = p["bc_y"] == 1
+    walls = p["bc_y"] in (1, 2)
     m = moments(f, g, p, walls)
     phi, ux, uy, rho = m["phi"], m["ux"], m["uy"], m["rho"]
     tau_f = p["tau_h"]
@@ -104,10 +114,12 @@ def step(f, g, phiu, p):
         gn[i] = np.roll(go[i], shift=(CY[i], CX[i]), axis=(0, 1))
     if walls:
         for i in range(9):
-            if CY[i] == 1:   # leaves through the top wall from the last row
+            if CY[i] == 1 and p["bc_y"] == 1:   # leaves through the top wall from the last row
                 fn[OPP[i], -1, :] = fo[i, -1, :]
                 gn[OPP[i], -1, :] = go[i, -1, :]
             if CY[i] == -1:  # leaves through the bottom wall from row 0
                 fn[OPP[i], 0, :] = fo[i, 0, :]
                 gn[OPP[i], 0, :] = go[i, 0, :]
+    if p["bc_y"] == 2:
+        _open_top(fn, gn)
     return fn, gn, np.stack([phi * ux, phi * uy])

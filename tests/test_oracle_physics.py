@@ -160,6 +160,34 @@ def test_single_phase_poiseuille():
     assert np.sqrt(((u - exact) ** 2).sum() / (exact ** 2).sum()) < 2e-3
 
 
+def test_open_top_half_poiseuille_first_order():
+    """Bottom wall and open top (bc_y = 2, the impact case's boundaries):
+    under a body force a single-phase layer tends to the lower half of a
+    channel of height 2 ny, u = G (2 H s - s^2) / (2 mu) with s = y + 1/2 and
+    H = ny, because the zero-gradient copy makes the top a symmetry line.
+    The copy is a first-order closure, so the L2 error halves as ny doubles
+    (measured 2.0% and 1.0% at ny = 16 and 32; a closed top is 79% off).
+    Catches copying the wrong directions or rows, or bouncing back at the top."""
+    errs = []
+    for ny in (16, 32):
+        P = dict(rho_l=1.0, rho_g=1.0, nu_l=0.1, nu_g=0.1, sigma=0.0, W=4.0, Gx=1e-6, bc_y=2)
+        lat = _lattice(4, ny, **P).init(np.ones((ny, 4)))
+        lat.step(int(4 * ny * ny / 0.1))
+        u = lat.fields()["ux"][:, 0]
+        s = np.arange(ny) + 0.5
+        exact = 1e-6 * (2 * ny * s - s * s) / (2 * 0.1)
+        errs.append(np.sqrt(((u - exact) ** 2).sum() / (exact ** 2).sum()))
+        assert abs(u[-1] / exact[-1] - 1) < 0.04      # no slip or reflection at the top
+    assert errs[0] < 0.025 and errs[1] < 0.0125
+    assert 1.8 < errs[0] / errs[1] < 2.2
+
+
+def test_open_top_needs_two_rows_and_known_bc():
+    for bc, ny in ((2, 1), (3, 8), (-1, 8)):
+        with pytest.raises(Exception):
+            _lattice(4, ny, bc_y=bc)
+
+
 def test_layered_poiseuille_table1_ratio10():
     """Layered Poiseuille flow at the paper's setup (100 x 10 -> 100 x 4, the
     flow is x-uniform), density ratio 10, step viscosity (Eq. 26).  Table 1
@@ -183,7 +211,7 @@ def test_layered_poiseuille_table1_ratio10():
     assert u[:ny // 2].max() < u[ny // 2:].max()   # the gas layer (upper) moves faster
 
 
-@pytest.mark.parametrize("bc_y", [0, 1])
+@pytest.mark.parametrize("bc_y", [0, 1, 2])
 def test_brute_force_numpy_transcription(bc_y):
     """8 x 8 grids, 10 steps, against the independent whole-array NumPy
     transcription (catches index and sign slips in either)."""
@@ -193,7 +221,7 @@ def test_brute_force_numpy_transcription(bc_y):
     ux0 = 0.01 * r.standard_normal((ny, nx))
     uy0 = 0.01 * r.standard_normal((ny, nx))
     p0 = 1e-4 * r.standard_normal((ny, nx))
-    P = dict(rho_l=1.0, rho_g=0.01, nu_l=0.05, nu_g=0.2, visc_mode=bc_y + 1 if bc_y else 0,
+    P = dict(rho_l=1.0, rho_g=0.01, nu_l=0.05, nu_g=0.2, visc_mode={0: 0, 1: 2, 2: 1}[bc_y],
              sigma=0.02, W=3.0, tau_h=0.9, Gx=1e-5, Gy=-2e-5, bc_y=bc_y)
     lat = _lattice(nx, ny, **P).init(phi0, ux0, uy0, p0)
     f, g, phiu = bn.init(phi0, ux0, uy0, p0, P)
@@ -206,7 +234,7 @@ def test_brute_force_numpy_transcription(bc_y):
     assert np.abs(of - f).max() < 1e-13
     assert np.abs(og - g).max() < 1e-15
     assert np.abs(ophiu - phiu).max() < 1e-15
-    m = bn.moments(f, g, P, bool(bc_y))
+    m = bn.moments(f, g, P, bc_y in (1, 2))
     F = lat.fields()
     for k in ("phi", "ux", "uy", "p", "mu"):
         assert np.abs(F[k] - m[k]).max() <= 1e-12 * max(1.0, np.abs(m[k]).max()), k
