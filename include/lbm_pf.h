@@ -9,9 +9,17 @@
  * ---------------------------------------
  *  - Grid: nx * ny nodes, node (x, y) at linear index y*nx + x (x fastest).
  *    Lattice units: dx = dt = 1, c_s^2 = 1/3 (Eq. 10).
- *  - x is always periodic.  y is periodic (bc_y = LBM_BC_PERIODIC) or closed
+ *  - x is always periodic.  y is periodic (bc_y = LBM_BC_PERIODIC), closed
  *    by half-way bounce-back walls at y = -1/2 and y = ny - 1/2
- *    (LBM_BC_WALLS; Sec. III B and III D).
+ *    (LBM_BC_WALLS; Sec. III B), or closed by the bottom wall only with an
+ *    open top (LBM_BC_WALL_OPEN; the impact case of Sec. III D, whose "open
+ *    boundary" the paper does not define).  The open top is read as a
+ *    zero-gradient outflow: populations leaving through it are lost, the top
+ *    row's incoming populations (c_y = -1) take the values of the row below,
+ *    and the phi stencil's ghost row repeats the top row.  It needs ny >= 2,
+ *    and the rule also holds for the initial state and for a restored one
+ *    (the top row's c_y = -1 populations of a state passed to lbm_set_state
+ *    are replaced by the row below's).
  *  - Host arrays passed in or out are double precision, N = nx*ny entries,
  *    owned by the caller; the library copies them and keeps no pointer.
  *  - All device memory is owned by the handle: allocated by lbm_create,
@@ -50,7 +58,7 @@ enum {
     LBM_VISC_STEP_MU = 2     /* mu = rho_l nu_l if phi >= 1/2 else rho_g nu_g,
                                 nu = mu / rho(phi)                        Eq. 26 */
 };
-enum { LBM_BC_PERIODIC = 0, LBM_BC_WALLS = 1 };
+enum { LBM_BC_PERIODIC = 0, LBM_BC_WALLS = 1, LBM_BC_WALL_OPEN = 2 };
 /* unit normal n of the sharpening term (normal_scheme) */
 enum {
     LBM_NORMAL_CENTRAL = 0, /* n = grad phi / |grad phi|, grad by Eq. 27  (Eq. 2) */
@@ -81,7 +89,7 @@ typedef struct {
     double tau_h;         /* Allen-Cahn relaxation time (tau_f of Eq. 8); > 1/2;
                              mobility M = (tau_h - 1/2)/3 (Eq. 14) */
     double Gx, Gy;        /* body-force density G (Eqs. 4b, 19), same in both phases */
-    int bc_y;             /* LBM_BC_PERIODIC or LBM_BC_WALLS */
+    int bc_y;             /* LBM_BC_PERIODIC, LBM_BC_WALLS or LBM_BC_WALL_OPEN */
     int normal_scheme;    /* LBM_NORMAL_* */
     int storage;          /* LBM_STORE_*: how populations are stored between steps */
     int check_every;      /* > 0: every check_every steps lbm_step synchronises the

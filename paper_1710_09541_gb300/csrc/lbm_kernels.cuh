@@ -47,7 +47,8 @@ struct Model {
     float inv_nu_l, inv_nu_g; // Eq. 25
     float mu_l, mu_g;       // Eq. 26
     int visc_mode;
-    int walls;              // half-way bounce-back walls in y
+    int walls;              // y boundary: 0 periodic, 1 bounce-back walls at both
+                            // ends, 2 bounce-back wall at y = 0 and an open top
     int local_normal;       // Eq. 29 instead of Eq. 2 with Eq. 27
 };
 
@@ -58,21 +59,27 @@ struct Nbr {
     bool lo, hi;      // node touches the wall at y = -1/2 / y = ny - 1/2
 };
 
-// WALLS < 0: decided at run time from `walls`; 0/1: fixed at compile time.
+// `walls` is the y-boundary code of Model::walls.  WALLS < 0: everything
+// decided at run time; 0: periodic, fixed at compile time; 1: a wall at y = 0
+// fixed at compile time, the kind of top (wall or open) read from `walls`.
+// At the open top the links that would enter from outside (c_y = -1) pull
+// from the top row itself, i.e. they take the values the row below pulls
+// (zero-gradient outflow); links leaving through it are not pulled by anyone.
 template <int WALLS = -1>
 __device__ __forceinline__ Nbr make_nbr(int x, int y, int nx, int ny, int walls) {
-    if (WALLS >= 0) walls = WALLS;
+    const bool walled = WALLS >= 0 ? WALLS != 0 : walls != 0;
+    const bool open_top = walled && walls == 2;
     Nbr q;
     q.x = x;
     q.xm = (x == 0) ? nx - 1 : x - 1;
     q.xp = (x == nx - 1) ? 0 : x + 1;
     const int ym = (y == 0) ? ny - 1 : y - 1;
-    const int yp = (y == ny - 1) ? 0 : y + 1;
+    const int yp = (y == ny - 1) ? (open_top ? y : 0) : y + 1;
     q.r0 = y * nx;
     q.rm = ym * nx;
     q.rp = yp * nx;
-    q.lo = walls && (y == 0);
-    q.hi = walls && (y == ny - 1);
+    q.lo = walled && (y == 0);
+    q.hi = walled && !open_top && (y == ny - 1);
     return q;
 }
 
@@ -161,7 +168,7 @@ __device__ __forceinline__ float sum8(const float v[9]) {
 __device__ __forceinline__ float sum9(const float v[9]) { return add(v[0], sum8(v)); }
 
 // coordinate of a tile/halo slot folded into the grid: periodic wrap in x;
-// in y wrap, or clamp at a wall (mirror ghost phi(-1) = phi(0)).
+// in y wrap, or clamp at a wall or the open top (ghost row = edge row).
 __device__ __forceinline__ int fold_x(int x, int nx) {
     if ((unsigned)x >= (unsigned)nx) x = ((x % nx) + nx) % nx;
     return x;

@@ -71,7 +71,8 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
                                           float* __restrict__ gd, float* __restrict__ phiu,
                                           unsigned int* __restrict__ flag, double* __restrict__ out,
                                           int nx, int ny, Model m, int x0, int y0) {
-    if (WALLS >= 0) m.walls = WALLS;
+    if (WALLS == 0) m.walls = 0;  // WALLS == 1 keeps the kind of top (wall or open)
+    const int wfold = WALLS >= 0 ? WALLS : m.walls;  // y folding: wrap (0) or clamp
     const size_t N = (size_t)nx * ny;
     const int N32 = (int)N;  // 20 N < 2^31 (checked at create): 32-bit offsets
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -95,13 +96,13 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
         sphi[ty + 1][tx + 1] = sum9(f);
     } else {
         sphi[ty + 1][tx + 1] =
-            phi_at_st<ST, WALLS>(fs, N32, fold_x(x, nx), fold_y(y, ny, m.walls), nx, ny, m.walls);
+            phi_at_st<ST, WALLS>(fs, N32, fold_x(x, nx), fold_y(y, ny, wfold), nx, ny, m.walls);
     }
     for (int r = ty * TX + tx; r < Ring<TX, TY>::count; r += TX * TY) {
         int lx, ly;
         Ring<TX, TY>::pos(r, lx, ly);
         sphi[ly + 1][lx + 1] = phi_at_st<ST, WALLS>(fs, N32, fold_x(x0 + lx, nx),
-                                                    fold_y(y0 + ly, ny, m.walls), nx, ny, m.walls);
+                                                    fold_y(y0 + ly, ny, wfold), nx, ny, m.walls);
     }
     __syncthreads();
     if (!active) return;
@@ -412,7 +413,10 @@ static lbm_status validate(int nx, int ny, const lbm_params* p, char* msg, size_
     if (!(p->W > 0)) return bad("W must be > 0");
     if (!(p->tau_h > 0.5)) return bad("tau_h must be > 0.5");
     if (!std::isfinite(p->Gx) || !std::isfinite(p->Gy)) return bad("G must be finite");
-    if (p->bc_y != LBM_BC_PERIODIC && p->bc_y != LBM_BC_WALLS) return bad("bc_y must be 0 or 1");
+    if (p->bc_y != LBM_BC_PERIODIC && p->bc_y != LBM_BC_WALLS && p->bc_y != LBM_BC_WALL_OPEN)
+        return bad("bc_y must be LBM_BC_PERIODIC, LBM_BC_WALLS or LBM_BC_WALL_OPEN");
+    if (p->bc_y == LBM_BC_WALL_OPEN && ny < 2)
+        return bad("LBM_BC_WALL_OPEN needs ny >= 2 (the open top repeats the row below)");
     if (p->normal_scheme != LBM_NORMAL_CENTRAL && p->normal_scheme != LBM_NORMAL_LOCAL)
         return bad("normal_scheme must be 0 or 1");
     if (p->storage != LBM_STORE_FP32 && p->storage != LBM_STORE_FP16_SHIFTED &&
@@ -423,6 +427,8 @@ static lbm_status validate(int nx, int ny, const lbm_params* p, char* msg, size_
         return bad("kernel must be LBM_KERNEL_AUTO, _GENERIC or _TMA");
     if (p->kernel == LBM_KERNEL_TMA && p->storage != LBM_STORE_FP32)
         return bad("LBM_KERNEL_TMA stages FP32 populations only");
+    if (p->kernel == LBM_KERNEL_TMA && p->bc_y == LBM_BC_WALL_OPEN)
+        return bad("LBM_KERNEL_TMA supports periodic and walled y boundaries only");
     if (p->kernel == LBM_KERNEL_TMA && !(nx % 4 == 0 && nx >= 72 && ny >= 20))
         return bad("LBM_KERNEL_TMA needs nx % 4 == 0 (16-byte row pitch), nx >= 72 and ny >= 20 "
                    "(the staged box fits in the grid)");
@@ -447,7 +453,7 @@ static Model make_model(const lbm_params& p) {
     m.mu_l = (float)(p.rho_l * p.nu_l);
     m.mu_g = (float)(p.rho_g * p.nu_g);
     m.visc_mode = p.visc_mode;
-    m.walls = p.bc_y == LBM_BC_WALLS;
+    m.walls = p.bc_y;  // 0 periodic, 1 walls, 2 wall and open top
     m.local_normal = p.normal_scheme == LBM_NORMAL_LOCAL;
     return m;
 }

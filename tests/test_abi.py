@@ -58,7 +58,7 @@ def test_params_struct_layout_matches_header(tmp_path):
 
 @pytest.mark.parametrize("bad", [
     dict(rho_g=0.0), dict(nu_l=-1.0), dict(visc_mode=3), dict(W=0.0), dict(tau_h=0.5),
-    dict(sigma=-1.0), dict(bc_y=2), dict(normal_scheme=5), dict(storage=7), dict(check_every=-1),
+    dict(sigma=-1.0), dict(bc_y=3), dict(bc_y=-1), dict(bc_y=2, kernel=2), dict(normal_scheme=5), dict(storage=7), dict(check_every=-1),
     dict(Gx=float("inf")),
 ])
 def test_create_rejects_bad_parameters(L, bad):
@@ -73,6 +73,23 @@ def test_create_rejects_bad_sizes(L, nx, ny):
     p = lbm.make_params()
     h = ctypes.c_void_p()
     assert L.lbm_create(nx, ny, ctypes.byref(p), ctypes.byref(h)) == lbm.LBM_ERR_INVALID
+
+
+def test_open_top_needs_two_rows(L):
+    p = lbm.make_params(bc_y=lbm.LBM_BC_WALL_OPEN)
+    h = ctypes.c_void_p()
+    assert L.lbm_create(16, 1, ctypes.byref(p), ctypes.byref(h)) == lbm.LBM_ERR_INVALID
+    assert not h.value
+
+
+def test_header_enum_values_match_the_binding():
+    import re
+    text = open(os.path.join(ROOT, "include", "lbm_pf.h")).read()
+    for name in ("LBM_BC_PERIODIC", "LBM_BC_WALLS", "LBM_BC_WALL_OPEN", "LBM_STORE_FP32",
+                 "LBM_STORE_FP16_SHIFTED", "LBM_STORE_BF16_SHIFTED", "LBM_KERNEL_AUTO",
+                 "LBM_KERNEL_GENERIC", "LBM_KERNEL_TMA"):
+        m = re.search(name + r"\s*=\s*(\d+)", text)
+        assert m and int(m.group(1)) == getattr(lbm, name), name
 
 
 def test_null_handle_calls_are_rejected(L):

@@ -86,8 +86,8 @@ def _one_step_parity(lbm, nx, ny, P, state, R=None):
     st64 = [a.astype(np.float64) for a in st32]
     o = oracle.Lattice(nx, ny, **P).set_state(*st64)
     pre = o.fields()
-    walls = P.get("bc_y", 0) == 1
-    gx, gy, _ = oracle.grad_lap(pre["phi"], bc_y=int(walls))
+    walls = P.get("bc_y", 0) in (1, 2)   # stencil rows clamp at a wall and at the open top
+    gx, gy, _ = oracle.grad_lap(pre["phi"], bc_y=P.get("bc_y", 0))
     lam = np.abs(4 * pre["phi"] * (1 - pre["phi"]) / P["W"])
     gmag = np.hypot(gx, gy)
     local = P.get("normal_scheme", 0) == 1
@@ -153,6 +153,9 @@ TRAJ_CASES = {
                                lambda: (cases.spinodal(128, 128, 0.5, 0.01, seed=12345),)),
     "local_normal_drop": (64, 48, dict(cases.params_static_drop(), normal_scheme=1),
                           lambda: (cases.drop(64, 48, 12, 4.0),)),
+    # the impact's bottom wall and open top (bc_y = 2), scaled to D = 24
+    "impact_open_top": (96, 64, dict(cases.params_impact(D=24.0, Re=100.0), bc_y=2),
+                        lambda: cases.impact(96, 64, 24.0, 2.4, 0.04, 5.0)),
 }
 
 
@@ -235,7 +238,8 @@ def test_free_run_walls_drop(lbm, mode):
     _assert_fields(got, ref, _scales(P, R=12))
 
 
-@pytest.mark.parametrize("nx,ny,bc", [(1, 1, 0), (3, 5, 0), (8, 8, 1), (33, 17, 0), (5, 2, 1), (31, 16, 1)])
+@pytest.mark.parametrize("nx,ny,bc", [(1, 1, 0), (3, 5, 0), (8, 8, 1), (33, 17, 0), (5, 2, 1), (31, 16, 1),
+                                      (8, 8, 2), (5, 2, 2), (31, 16, 2), (3, 40, 2)])
 def test_free_run_tiny_and_degenerate_grids(lbm, nx, ny, bc):
     """Grids smaller than one tile, one-node-wide grids, walls two rows apart."""
     P = dict(rho_l=1.0, rho_g=0.1, nu_l=0.1, nu_g=0.1, visc_mode=0, sigma=0.01, W=3.0,
@@ -247,9 +251,10 @@ def test_free_run_tiny_and_degenerate_grids(lbm, nx, ny, bc):
     _assert_fields(got, ref, {"phi": 1.0, "rho": 1.0, "ux": 1e-3, "uy": 1e-3, "p": 1e-3})
 
 
-def test_init_state_matches_oracle(lbm):
+@pytest.mark.parametrize("bc", [1, 2])
+def test_init_state_matches_oracle(lbm, bc):
     nx, ny = 37, 29
-    P = dict(cases.params_static_drop(), bc_y=1)
+    P = dict(cases.params_static_drop(), bc_y=bc)
     phi0 = cases.drop(nx, ny, 8, 4.0, walls_y=True)
     r = np.random.default_rng(1)
     ux0, uy0, p0 = (1e-3 * r.standard_normal((ny, nx)) for _ in range(3))
@@ -339,13 +344,14 @@ def _spreading_radius(phi, film, W):
     return 0.5 * (right - left + 1)
 
 
-def test_impact_spreading_radius_scaled(lbm):
+@pytest.mark.parametrize("bc", [1, 2])
+def test_impact_spreading_radius_scaled(lbm, bc):
     """Droplet impact on a thin film, scaled to D = 40 on 480 x 120 (film
     0.1 D, U = 0.04, Re = 100, We = 8000, ratio 1000, mu ratio 40): the
     spreading radius agrees within 1% up to t* = t U / D = 1, and the full
     fields pointwise for the first 10 steps."""
     nx, ny, D, film = 480, 120, 40.0, 4.0
-    P = cases.params_impact(D=D, Re=100.0)
+    P = dict(cases.params_impact(D=D, Re=100.0), bc_y=bc)
     phi0, u0, v0 = cases.impact(nx, ny, D, film, 0.04, P["W"])
     got, ref = _free_run(lbm, nx, ny, P, 10, phi0, u0, v0)
     _assert_fields(got, ref, _scales(P, R=D / 2))
@@ -363,10 +369,11 @@ def test_impact_spreading_radius_scaled(lbm):
 
 # ------------------------------------------------------------ behaviour ----
 
-def test_checkpoint_resume_bit_exact(lbm):
+@pytest.mark.parametrize("bc", [0, 2])
+def test_checkpoint_resume_bit_exact(lbm, bc):
     nx, ny = 70, 50
-    P = cases.params_static_drop()
-    phi0 = cases.drop(nx, ny, 12, 4.0)
+    P = dict(cases.params_static_drop(), bc_y=bc)
+    phi0 = cases.drop(nx, ny, 12, 4.0, walls_y=bc > 0)
     with lbm.Lattice(nx, ny, **P) as a, lbm.Lattice(nx, ny, **P) as b:
         a.init(phi0).step(40)
         b.init(phi0).step(15)
