@@ -230,6 +230,33 @@ lbm_status lbm_batch_info(const lbm_batch* b, int cls, int* ncases, int* tile_tx
 void lbm_batch_destroy(lbm_batch* b);
 const char* lbm_batch_last_error(const lbm_batch* b);
 
+/*
+ * Impact-case tooling (Sec. III D).  Both read the current state on the device
+ * with the step's own arithmetic, so their values equal lbm_get_fields' at
+ * the same nodes bit for bit, and both block until the result is on the host.
+ *
+ * lbm_spreading_radius -- the spreading radius r of an impacting drop (the
+ *   quantity of Fig. 8, r/D against t U/D): half the x-extent of the run of
+ *   nodes with phi >= 1/2 that contains column xc on row y, counted in nodes
+ *   (x_right - x_left + 1) / 2; 0 when phi(xc, y) < 1/2.  The run does not
+ *   wrap around the periodic x edges.  The paper gives neither the row nor
+ *   the rule; the row is the caller's (the tests use the row W above the film
+ *   surface).  r_interp (may be NULL) places each end at the phi = 1/2
+ *   crossing by linear interpolation between the run's end node and its gas
+ *   neighbour (an end at the grid edge lies half a node beyond it).
+ *   Errors: LBM_ERR_INVALID (NULL handle, (xc, y) outside the grid),
+ *   LBM_ERR_STATE (before lbm_init), LBM_ERR_CUDA.
+ * lbm_probe -- phi, rho, u and p (Eqs. 12, 13, 22) at npts nodes (x[j], y[j]),
+ *   0 <= npts <= nx*ny, written to caller-owned host arrays of npts doubles
+ *   (any output may be NULL).  A Laplace pressure jump or a velocity at a few
+ *   nodes costs a few KB of traffic instead of a full read-back.
+ *   Errors: LBM_ERR_INVALID (NULL handle or coordinates, npts out of range, a
+ *   node outside the grid: nothing is written), LBM_ERR_STATE, LBM_ERR_CUDA.
+ */
+lbm_status lbm_spreading_radius(lbm_handle* h, int y, int xc, double* r, double* r_interp);
+lbm_status lbm_probe(lbm_handle* h, int npts, const int* x, const int* y, double* phi, double* rho,
+                     double* ux, double* uy, double* p);
+
 /* lbm_synchronize -- wait for all work enqueued by this handle. */
 lbm_status lbm_synchronize(lbm_handle* h);
 

@@ -1296,3 +1296,153 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Impact-case tooling: the spreading radius of Sec. III D (Fig. 8) and point
+// probes of the fields, both evaluated on the device from the current state
+// with the step's own arithmetic (phi by the same pull and sum, the fields by
+// the same stencil and recovery), so they equal lbm_get_fields bit for bit at
+// the nodes they touch.
+// ---------------------------------------------------------------------------
+namespace {
+
+// One block scans row y: the last column left of xc and the first column
+// right of xc where phi < 1/2 bound the liquid run through xc.
+// out = [r, r_interp, x_left, x_right].
+template <int ST>
+__global__ void k_spreading_radius(const void* __restrict__ fs, int nx, int ny, int walls, int y,
+                                   int xc, double* __restrict__ out) {
+    __shared__ int s_left, s_right;
+    const int N = nx * ny;
+    if (threadIdx.x == 0) {
+        s_left = -1;
+        s_right = nx;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+        if (x == xc) continue;
+        const float phi = phi_at_st<ST, -1>(fs, N, x, y, nx, ny, walls);
+        if (!(phi >= 0.5f)) {
+            if (x < xc) atomicMax(&s_left, x);
+            else atomicMin(&s_right, x);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    auto phi_of = [&](int x) { return (double)phi_at_st<ST, -1>(fs, N, x, y, nx, ny, walls); };
+    if (!(phi_of(xc) >= 0.5)) {
+        out[0] = out[1] = 0.0;
+        out[2] = out[3] = -1.0;
+        return;
+    }
+    const int xl = s_left + 1, xr = s_right - 1;
+    out[0] = 0.5 * (xr - xl + 1);
+    // phi = 1/2 crossings by linear interpolation between the run's end nodes
+    // and their gas neighbours; a run that reaches the grid edge ends half a
+    // node beyond it
+    double L = xl - 0.5, R = xr + 0.5;
+    if (s_left >= 0) {
+        const double a = phi_of(s_left), b = phi_of(xl);
+        L = s_left + (0.5 - a) / (b - a);
+    }
+    if (s_right < nx) {
+        const double a = phi_of(xr), b = phi_of(s_right);
+        R = xr + (a - 0.5) / (a - b);
+    }
+    out[1] = 0.5 * (R - L);
+    out[2] = xl;
+    out[3] = xr;
+}
+
+// Fields at npts nodes (xy = x0, y0, x1, y1, ...), planes out[k * npts + j]
+// for phi, rho, ux, uy, p.
+template <int ST>
+__global__ void k_probe(const void* __restrict__ fs, const void* __restrict__ gs, int nx, int ny,
+                        Model m, const int* __restrict__ xy, int npts, double* __restrict__ out) {
+    const int N = nx * ny;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < npts; j += gridDim.x * blockDim.x) {
+        const int x = xy[2 * j], y = xy[2 * j + 1];
+        float ph[3][3];
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx)
+                ph[dy + 1][dx + 1] = phi_at_st<ST, -1>(fs, N, fold_x(x + dx, nx),
+                                                       fold_y(y + dy, ny, m.walls), nx, ny, m.walls);
+        float g[9];
+        pull9g<ST>(gs, N, make_nbr(x, y, nx, ny, m.walls), g);
+        const float phi = ph[1][1];
+        const Stencil st = stencil(phi, ph[1][2], ph[1][0], ph[2][1], ph[0][1], ph[2][2], ph[2][0],
+                                   ph[0][0], ph[0][2]);
+        const Macro M = macroscopic(m, g, phi, st.gx, st.gy, st.lap);
+        out[j] = phi;
+        out[npts + j] = M.rho;
+        out[2 * npts + j] = M.ux;
+        out[3 * npts + j] = M.uy;
+        out[4 * npts + j] = M.p;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_spreading_radius(lbm_handle* h, int y, int xc, double* r, double* r_interp) {
+    if (!h) return LBM_ERR_INVALID;
+    if (!h->inited) return fail(h, LBM_ERR_STATE, "lbm_spreading_radius before lbm_init");
+    if (y < 0 || y >= h->ny || xc < 0 || xc >= h->nx)
+        return fail(h, LBM_ERR_INVALID, "lbm_spreading_radius: (xc, y) = (%d, %d) outside the grid",
+                    xc, y);
+    LBM_CUDA(h, cudaSetDevice(h->device));
+    auto k = h->prm.storage == LBM_STORE_FP16_SHIFTED   ? k_spreading_radius<ST_FP16>
+             : h->prm.storage == LBM_STORE_BF16_SHIFTED ? k_spreading_radius<ST_BF16>
+                                                        : k_spreading_radius<ST_FP32>;
+    k<<<1, 1024, 0, h->stream>>>(h->f[h->cur], h->nx, h->ny, h->model.walls, y, xc, h->red_res);
+    LBM_CUDA(h, cudaGetLastError());
+    double res[4];
+    LBM_CUDA(h, cudaMemcpyAsync(res, h->red_res, sizeof res, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (r) *r = res[0];
+    if (r_interp) *r_interp = res[1];
+    return LBM_OK;
+}
+
+lbm_status lbm_probe(lbm_handle* h, int npts, const int* x, const int* y, double* phi, double* rho,
+                     double* ux, double* uy, double* p) {
+    if (!h) return LBM_ERR_INVALID;
+    if (!h->inited) return fail(h, LBM_ERR_STATE, "lbm_probe before lbm_init");
+    if (npts < 0 || (size_t)npts > h->N)
+        return fail(h, LBM_ERR_INVALID, "lbm_probe: need 0 <= npts <= nx*ny, got %d", npts);
+    if (npts == 0) return LBM_OK;
+    if (!x || !y) return fail(h, LBM_ERR_INVALID, "lbm_probe: NULL coordinates");
+    std::vector<int> xy(2 * (size_t)npts);
+    for (int j = 0; j < npts; ++j) {
+        if (x[j] < 0 || x[j] >= h->nx || y[j] < 0 || y[j] >= h->ny)
+            return fail(h, LBM_ERR_INVALID, "lbm_probe: point %d = (%d, %d) outside the grid", j,
+                        x[j], y[j]);
+        xy[2 * j] = x[j];
+        xy[2 * j + 1] = y[j];
+    }
+    LBM_CUDA(h, cudaSetDevice(h->device));
+    // staging holds 80 B per node: 8 B of coordinates and 40 B of fields per point
+    int* d_xy = (int*)h->staging;
+    double* d_out = (double*)h->staging + h->N;
+    LBM_CUDA(h, cudaMemcpyAsync(d_xy, xy.data(), xy.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                h->stream));
+    auto k = h->prm.storage == LBM_STORE_FP16_SHIFTED   ? k_probe<ST_FP16>
+             : h->prm.storage == LBM_STORE_BF16_SHIFTED ? k_probe<ST_BF16>
+                                                        : k_probe<ST_FP32>;
+    const int blocks = (npts + 127) / 128 < 1184 ? (npts + 127) / 128 : 1184;
+    k<<<blocks, 128, 0, h->stream>>>(h->f[h->cur], h->g[h->cur], h->nx, h->ny, h->model, d_xy,
+                                      npts, d_out);
+    LBM_CUDA(h, cudaGetLastError());
+    double* outs[5] = {phi, rho, ux, uy, p};
+    for (int k5 = 0; k5 < 5; ++k5)
+        if (outs[k5])
+            LBM_CUDA(h, cudaMemcpyAsync(outs[k5], d_out + (size_t)k5 * npts, npts * sizeof(double),
+                                        cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -32,7 +32,8 @@ LBM_KERNEL_AUTO, LBM_KERNEL_GENERIC, LBM_KERNEL_TMA = 0, 1, 2
 EXPORTS = ("lbm_create", "lbm_init", "lbm_step", "lbm_get_fields", "lbm_state_bytes",
            "lbm_get_state", "lbm_set_state", "lbm_diag", "lbm_synchronize", "lbm_destroy",
            "lbm_last_error", "lbm_diag_fields_noalloc", "lbm_batch_create", "lbm_batch_step",
-           "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error")
+           "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error",
+           "lbm_spreading_radius", "lbm_probe")
 
 
 class LbmError(RuntimeError):
@@ -84,6 +85,9 @@ def load() -> ctypes.CDLL:
     L.lbm_last_error.argtypes = [vp]
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_diag_fields_noalloc.argtypes = [vp, sz, vp, vp, ctypes.c_char_p, sz]
+    L.lbm_spreading_radius.argtypes = [vp, i, i, pd, pd]
+    pi = ctypes.POINTER(ctypes.c_int)
+    L.lbm_probe.argtypes = [vp, i, pi, pi, pd, pd, pd, pd, pd]
     L.lbm_diag_fields_noalloc.restype = ctypes.c_int
     L.lbm_batch_create.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.lbm_batch_create.restype = ctypes.c_int
@@ -205,6 +209,26 @@ class Lattice:
         r = [ctypes.c_double() for _ in range(4)]
         self._check(self._L.lbm_diag(self._h, *(ctypes.byref(x) for x in r)))
         return tuple(x.value for x in r)
+
+    def spreading_radius(self, y: int, xc: int | None = None):
+        """(r, r_interp) on row y around column xc (default nx // 2)."""
+        r, ri = ctypes.c_double(), ctypes.c_double()
+        xc = self.nx // 2 if xc is None else int(xc)
+        self._check(self._L.lbm_spreading_radius(self._h, int(y), xc, ctypes.byref(r),
+                                                 ctypes.byref(ri)))
+        return r.value, ri.value
+
+    def probe(self, x, y):
+        """Fields at nodes (x[j], y[j]): dict of float64 arrays phi, rho, ux, uy, p."""
+        x = np.ascontiguousarray(x, dtype=np.int32).ravel()
+        y = np.ascontiguousarray(y, dtype=np.int32).ravel()
+        if x.shape != y.shape:
+            raise ValueError("x and y need the same length")
+        out = {k: np.empty(x.size, dtype=np.float64) for k in ("phi", "rho", "ux", "uy", "p")}
+        pi = ctypes.POINTER(ctypes.c_int)
+        self._check(self._L.lbm_probe(self._h, x.size, x.ctypes.data_as(pi), y.ctypes.data_as(pi),
+                                      *(_dptr(out[k]) for k in ("phi", "rho", "ux", "uy", "p"))))
+        return out
 
     def synchronize(self):
         self._check(self._L.lbm_synchronize(self._h))

@@ -97,4 +97,6 @@ def test_null_handle_calls_are_rejected(L):
     assert L.lbm_get_fields(None, None, None, None, None, None) == lbm.LBM_ERR_INVALID
     assert L.lbm_diag(None, None, None, None, None) == lbm.LBM_ERR_INVALID
     assert L.lbm_state_bytes(None) == 0
+    assert L.lbm_spreading_radius(None, 0, 0, None, None) == lbm.LBM_ERR_INVALID
+    assert L.lbm_probe(None, 0, None, None, None, None, None, None, None) == lbm.LBM_ERR_INVALID
     L.lbm_destroy(None)
