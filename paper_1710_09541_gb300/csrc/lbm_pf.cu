@@ -63,6 +63,20 @@ struct Ring {
 #ifndef LBM_STEP_MINB
 #define LBM_STEP_MINB 4
 #endif
+// load (phi u) of the previous step with the node's pulls instead of just
+// before the collision
+#ifndef LBM_EARLY_PHIU
+#define LBM_EARLY_PHIU 1
+#endif
+// L2 prefetch distance of the step kernel in tiles, per 10 SMs (0: off);
+// 15 = 1.5 tiles per SM, about a third of a resident wave at 4 blocks/SM
+#ifndef LBM_PREFETCH_PER10SM
+#define LBM_PREFETCH_PER10SM 15
+#endif
+// grids with fewer tiles than this many prefetch distances step without it
+#ifndef LBM_PREFETCH_MIN_TILES_X
+#define LBM_PREFETCH_MIN_TILES_X 16
+#endif
 // One TX x TY tile with origin (x0, y0): the body shared by the single-case
 // step kernel and the batched persistent kernel (so both give the same bits).
 template <int TX, int TY, bool FIELDS, int WALLS, int ST>
@@ -84,8 +98,14 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
     // thread on the first threads so only the first warps take that path.
     float f[9], g[9];
     Nbr q;
+#if LBM_EARLY_PHIU
+    float2 prev = make_float2(0.f, 0.f);
+#endif
     if (active) {
         q = make_nbr<WALLS>(x, y, nx, ny, m.walls);
+#if LBM_EARLY_PHIU
+        if (!FIELDS) prev = make_float2(phiu[q.r0 + x], phiu[N32 + q.r0 + x]);
+#endif
         if constexpr (ST == ST_FP32) {  // the plain float pull (measured 2% faster)
             pull9(fs, N, q, f);
             pull9(gs, N, q, g);
@@ -126,19 +146,57 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
     // one test: a NaN or Inf in any of phi, u, p makes the sum non-finite
     if (!isfinite(add(add(phi, M.ux), add(M.uy, M.p)))) atomicOr(flag, 1u);
 
+#if !LBM_EARLY_PHIU
     const float2 prev = make_float2(phiu[n32], phiu[N32 + n32]);
+#endif
     const float2 now = collide(m, f, g, phi, st, M, prev);
     phiu[n32] = now.x;
     phiu[N32 + n32] = now.y;
     Pop<ST>::stfg(fd, gd, N32, n32, f, g, phi);
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Ask L2 for the rows tile (bx, by) will pull: rows by*TY - 1 .. by*TY + TY
+// of the 18 population planes and the TY rows of (phi u), from column bx*TX
+// (one request per row and plane).  Called by a block for the tile that
+// starts about one resident wave after it, so those DRAM reads are in
+// flight while the current tiles compute: the step is bound by load latency,
+// and a prefetch holds no register and no shared memory.
+template <int TX, int TY, int ST>
+__device__ __forceinline__ void prefetch_tile(const void* fs, const void* gs, const float* phiu,
+                                              int nx, int ny, int wfold, int bx, int by) {
+    const int N = nx * ny;
+    const int t = threadIdx.y * TX + threadIdx.x;
+    const int x0 = bx * TX;
+    for (int k = t; k < 18 * (TY + 2); k += TX * TY) {
+        const int plane = k / (TY + 2), r = k % (TY + 2);
+        const int idx = fold_y(by * TY - 1 + r, ny, wfold) * nx + x0;
+        prefetch_l2(plane < 9 ? Pop<ST>::addr_f(fs, N, plane, idx) : Pop<ST>::addr_g(gs, N, plane - 9, idx));
+    }
+    for (int k = t; k < 2 * TY; k += TX * TY) {
+        const int yy = by * TY + (k % TY);
+        if (yy < ny) prefetch_l2(phiu + ((k / TY) * N + yy * nx + x0));
+    }
+}
+
 template <int TX, int TY, bool FIELDS, int WALLS, int ST>
 __global__ void __launch_bounds__(TX* TY, LBM_STEP_MINB)
     k_step(const float* __restrict__ fs, const float* __restrict__ gs, float* __restrict__ fd,
            float* __restrict__ gd, float* __restrict__ phiu, unsigned int* __restrict__ flag,
-           double* __restrict__ out, int nx, int ny, Model m) {
+           double* __restrict__ out, int nx, int ny, Model m, int pf_ahead) {
     __shared__ float sphi[TY + 2][TX + 2];
+    // FP32 storage only: the 16-bit steps are instruction-bound, and there
+    // the prefetch requests cost more than they hide (measured 43.6 k ->
+    // 41.0 k MLUPS at 2048^2 for FP16)
+    if (!FIELDS && ST == ST_FP32 && pf_ahead > 0) {
+        const int lin = blockIdx.y * gridDim.x + blockIdx.x + pf_ahead;
+        if (lin < gridDim.x * gridDim.y)
+            prefetch_tile<TX, TY, ST>(fs, gs, phiu, nx, ny, WALLS >= 0 ? WALLS : m.walls,
+                                      lin % gridDim.x, lin / gridDim.x);
+    }
     step_tile<TX, TY, FIELDS, WALLS, ST>(sphi, fs, gs, fd, gd, phiu, flag, out, nx, ny, m,
                                          blockIdx.x * TX, blockIdx.y * TY);
 }
@@ -375,6 +433,7 @@ struct lbm_handle {
     long long since_check = 0;
     // TMA-staged step kernel (used when kernel != LBM_KERNEL_GENERIC and nx % 4 == 0)
     bool use_tma = false;
+    int pf_ahead = 0;  // L2 prefetch distance of the step kernel, in tiles
     CUtensorMap tm_f[2], tm_g[2], tm_u;
     int tiles_x = 0, ntiles = 0, tma_grid = 0;
     char err[512] = {0};
@@ -490,7 +549,7 @@ static lbm_status launch_step(lbm_handle* h, bool fields, double* out) {
     dim3 block(STEP_TX, STEP_TY);
     dim3 grid((h->nx + STEP_TX - 1) / STEP_TX, (h->ny + STEP_TY - 1) / STEP_TY);
     using K = void (*)(const float*, const float*, float*, float*, float*, unsigned int*, double*,
-                       int, int, Model);
+                       int, int, Model, int);
     K k;
     switch (h->prm.storage) {
         case LBM_STORE_FP16_SHIFTED:
@@ -510,10 +569,10 @@ static lbm_status launch_step(lbm_handle* h, bool fields, double* out) {
     }
     if (fields)
         k<<<grid, block, 0, h->stream>>>(h->f[c], h->g[c], nullptr, nullptr, h->phiu, h->flag, out,
-                                         h->nx, h->ny, h->model);
+                                         h->nx, h->ny, h->model, 0);
     else
         k<<<grid, block, 0, h->stream>>>(h->f[c], h->g[c], h->f[c ^ 1], h->g[c ^ 1], h->phiu,
-                                         h->flag, nullptr, h->nx, h->ny, h->model);
+                                         h->flag, nullptr, h->nx, h->ny, h->model, h->pf_ahead);
     LBM_CUDA(h, cudaGetLastError());
     if (!fields) h->cur ^= 1;
     return LBM_OK;
@@ -624,6 +683,14 @@ lbm_status lbm_create(int nx, int ny, const lbm_params* p, lbm_handle** out) {
     if (e == cudaSuccess) e = cudaMalloc(&h->flag, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->pf_ahead = LBM_PREFETCH_PER10SM * sms / 10;
+    {
+        // on grids of a few waves the prefetched tile is often already running
+        const long long tiles = (long long)((nx + STEP_TX - 1) / STEP_TX) * ((ny + STEP_TY - 1) / STEP_TY);
+        if (tiles < (long long)LBM_PREFETCH_MIN_TILES_X * h->pf_ahead) h->pf_ahead = 0;
+    }
     if (e != cudaSuccess) {
         fprintf(stderr, "lbm_create: %s\n", cudaGetErrorString(e));
         release(h);
@@ -631,8 +698,9 @@ lbm_status lbm_create(int nx, int ny, const lbm_params* p, lbm_handle** out) {
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
     }
-    // LBM_KERNEL_AUTO takes the direct-load kernel: on GB300 it measured 128 us
-    // per 2048^2 step against 201 us for the TMA-staged one
+    // LBM_KERNEL_AUTO takes the direct-load kernel: on GB300 it measured 110 us
+    // per 2048^2 step (with L2 prefetch; 128 us without) against 201 us for the
+    // TMA-staged one
     if (p->kernel == LBM_KERNEL_TMA) {
         lbm_status ts = setup_tma(h);
         if (ts != LBM_OK) {

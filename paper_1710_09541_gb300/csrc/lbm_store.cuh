@@ -71,6 +71,13 @@ struct Pop<ST_FP32> {
         static_cast<float*>(b)[i * N + idx] = v;
     }
     __device__ static float round_f(int, float v) { return v; }
+    // address of entry idx of plane i (for prefetches)
+    __device__ static const void* addr_f(const void* b, int N, int i, int idx) {
+        return static_cast<const float*>(b) + (i * N + idx);
+    }
+    __device__ static const void* addr_g(const void* b, int N, int i, int idx) {
+        return addr_f(b, N, i, idx);
+    }
 };
 
 template <typename H>
@@ -159,6 +166,14 @@ struct Shifted16 {
     }
     // the value a moving population takes after storage
     __device__ static float round_f(int i, float v) { return i == 0 ? v : dec_f(i, enc_f(i, v)); }
+    // address of entry idx of plane i (for prefetches)
+    __device__ static const void* addr_f(const void* b, int N, int i, int idx) {
+        if (i == 0) return static_cast<const float*>(b) + idx;
+        return fh(b, N) + ((i - 1) * N + idx);
+    }
+    __device__ static const void* addr_g(const void* b, int N, int i, int idx) {
+        return static_cast<const unsigned short*>(b) + (i * N + idx);
+    }
 };
 
 template <>
