@@ -168,16 +168,16 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 template <int TX, int TY, int ST>
 __device__ __forceinline__ void prefetch_tile(const void* fs, const void* gs, const float* phiu,
                                               int nx, int ny, int wfold, int bx, int by) {
+    static_assert(18 * (TY + 2) + 2 * TY <= TX * TY, "one request per thread");
     const int N = nx * ny;
     const int t = threadIdx.y * TX + threadIdx.x;
     const int x0 = bx * TX;
-    for (int k = t; k < 18 * (TY + 2); k += TX * TY) {
-        const int plane = k / (TY + 2), r = k % (TY + 2);
+    if (t < 18 * (TY + 2)) {
+        const int plane = t / (TY + 2), r = t - plane * (TY + 2);
         const int idx = fold_y(by * TY - 1 + r, ny, wfold) * nx + x0;
         prefetch_l2(plane < 9 ? Pop<ST>::addr_f(fs, N, plane, idx) : Pop<ST>::addr_g(gs, N, plane - 9, idx));
-    }
-    for (int k = t; k < 2 * TY; k += TX * TY) {
-        const int yy = by * TY + (k % TY);
+    } else if (t < 18 * (TY + 2) + 2 * TY) {
+        const int k = t - 18 * (TY + 2), yy = by * TY + (k % TY);
         if (yy < ny) prefetch_l2(phiu + ((k / TY) * N + yy * nx + x0));
     }
 }
