@@ -106,13 +106,7 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
 #if LBM_EARLY_PHIU
         if (!FIELDS) prev = make_float2(phiu[q.r0 + x], phiu[N32 + q.r0 + x]);
 #endif
-        if constexpr (ST == ST_FP32) {  // the plain float pull (measured 2% faster)
-            pull9(fs, N, q, f);
-            pull9(gs, N, q, g);
-        } else {
-            pull9f<ST, WALLS>(fs, N32, q, f);
-            pull9g<ST, WALLS>(gs, N32, q, g);
-        }
+        pull18<ST, WALLS>(fs, gs, N32, q, f, g);
         sphi[ty + 1][tx + 1] = sum9(f);
     } else {
         sphi[ty + 1][tx + 1] =
@@ -165,8 +159,8 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 // starts about one resident wave after it, so those DRAM reads are in
 // flight while the current tiles compute: the step is bound by load latency,
 // and a prefetch holds no register and no shared memory.
-template <int TX, int TY, int ST>
-__device__ __forceinline__ void prefetch_tile(const void* fs, const void* gs, const float* phiu,
+template <int TX, int TY>
+__device__ __forceinline__ void prefetch_tile(const float* fs, const float* gs, const float* phiu,
                                               int nx, int ny, int wfold, int bx, int by) {
     static_assert(18 * (TY + 2) + 2 * TY <= TX * TY, "one request per thread");
     const int N = nx * ny;
@@ -175,7 +169,7 @@ __device__ __forceinline__ void prefetch_tile(const void* fs, const void* gs, co
     if (t < 18 * (TY + 2)) {
         const int plane = t / (TY + 2), r = t - plane * (TY + 2);
         const int idx = fold_y(by * TY - 1 + r, ny, wfold) * nx + x0;
-        prefetch_l2(plane < 9 ? Pop<ST>::addr_f(fs, N, plane, idx) : Pop<ST>::addr_g(gs, N, plane - 9, idx));
+        prefetch_l2(plane < 9 ? fs + (plane * N + idx) : gs + ((plane - 9) * N + idx));
     } else if (t < 18 * (TY + 2) + 2 * TY) {
         const int k = t - 18 * (TY + 2), yy = by * TY + (k % TY);
         if (yy < ny) prefetch_l2(phiu + ((k / TY) * N + yy * nx + x0));
@@ -191,11 +185,13 @@ __global__ void __launch_bounds__(TX* TY, LBM_STEP_MINB)
     // FP32 storage only: the 16-bit steps are instruction-bound, and there
     // the prefetch requests cost more than they hide (measured 43.6 k ->
     // 41.0 k MLUPS at 2048^2 for FP16)
-    if (!FIELDS && ST == ST_FP32 && pf_ahead > 0) {
-        const int lin = blockIdx.y * gridDim.x + blockIdx.x + pf_ahead;
-        if (lin < gridDim.x * gridDim.y)
-            prefetch_tile<TX, TY, ST>(fs, gs, phiu, nx, ny, WALLS >= 0 ? WALLS : m.walls,
+    if constexpr (!FIELDS && ST == ST_FP32) {
+        if (pf_ahead > 0) {
+            const int lin = blockIdx.y * gridDim.x + blockIdx.x + pf_ahead;
+            if (lin < gridDim.x * gridDim.y)
+                prefetch_tile<TX, TY>(fs, gs, phiu, nx, ny, WALLS >= 0 ? WALLS : m.walls,
                                       lin % gridDim.x, lin / gridDim.x);
+        }
     }
     step_tile<TX, TY, FIELDS, WALLS, ST>(sphi, fs, gs, fd, gd, phiu, flag, out, nx, ny, m,
                                          blockIdx.x * TX, blockIdx.y * TY);
@@ -240,7 +236,7 @@ __global__ void k_init(const double* __restrict__ in, void* __restrict__ fd,
                 eq_at(in, N, (size_t)ys * nx + xs, j, m, fe, ge);
             }
             Pop<ST>::putf(fd, N32, j, (int)n, fe);
-            Pop<ST>::putg(gd, N32, j, (int)n, ge);
+            Pop<ST>::putg(fd, gd, N32, j, (int)n, ge);
         }
         const float phi = (float)in[n];
         {
@@ -270,13 +266,13 @@ __global__ void k_state_out(const void* __restrict__ fs, const void* __restrict_
          n += (size_t)gridDim.x * blockDim.x) {
         const int x = (int)(n % nx), y = (int)(n / nx);
         const Nbr q = make_nbr(x, y, nx, ny, walls);
-        float v[9];
-        pull9f<ST>(fs, N32, q, v);
+        float v[9], w[9];
+        pull18<ST>(fs, gs, N32, q, v, w);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) st[i * N + n] = v[i];
-        pull9g<ST>(gs, N32, q, v);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) st[(9 + i) * N + n] = v[i];
+        for (int i = 0; i < 9; ++i) {
+            st[i * N + n] = v[i];
+            st[(9 + i) * N + n] = w[i];
+        }
         st[18 * N + n] = phiu[n];
         st[19 * N + n] = phiu[N + n];
     }
@@ -308,7 +304,7 @@ __global__ void k_state_in(const float* __restrict__ st, void* __restrict__ fd,
                 dir = j;
             }
             Pop<ST>::putf(fd, N32, j, (int)n, st[dir * N + src]);
-            Pop<ST>::putg(gd, N32, j, (int)n, st[(9 + dir) * N + src]);
+            Pop<ST>::putg(fd, gd, N32, j, (int)n, st[(9 + dir) * N + src]);
         }
         {
             float c = st[n];
@@ -1437,8 +1433,8 @@ __global__ void k_probe(const void* __restrict__ fs, const void* __restrict__ gs
             for (int dx = -1; dx <= 1; ++dx)
                 ph[dy + 1][dx + 1] = phi_at_st<ST, -1>(fs, N, fold_x(x + dx, nx),
                                                        fold_y(y + dy, ny, m.walls), nx, ny, m.walls);
-        float g[9];
-        pull9g<ST>(gs, N, make_nbr(x, y, nx, ny, m.walls), g);
+        float f[9], g[9];
+        pull18<ST>(fs, gs, N, make_nbr(x, y, nx, ny, m.walls), f, g);
         const float phi = ph[1][1];
         const Stencil st = stencil(phi, ph[1][2], ph[1][0], ph[2][1], ph[0][1], ph[2][2], ph[2][0],
                                    ph[0][0], ph[0][2]);

@@ -5,16 +5,22 @@
 //     f_0 is written as phi - sum_{i>0} f_i (see below).
 //
 //   FP16 / BF16 shifted (LBM_STORE_FP16_SHIFTED, LBM_STORE_BF16_SHIFTED):
-//     f_0          FP32 plane, written as phi - sum_{i>0} decode(encode(f_i)):
-//                  the rest population absorbs the rounding of the eight
-//                  moving ones, so the stored populations of a node sum to its
-//                  phi up to FP32 round-off and sum phi stays conserved.
-//     f_1..f_8     16-bit planes of f_i / w_i - 1/2: the offset from the
+//     f_0          FP32, written as phi - sum_{i>0} decode(encode(f_i)): the
+//                  rest population absorbs the rounding of the eight moving
+//                  ones, so the stored populations of a node sum to its phi up
+//                  to FP32 round-off and sum phi stays conserved.
+//     f_1..f_8     16-bit codes of f_i / w_i - 1/2: the offset from the
 //                  weight-scaled rest state at phi_ref = 1/2 (phi lies in [0, 1]).
-//     g_0..g_8     16-bit planes of S g_i / w_i (p_ref = 0), with S = 2^10 for
+//     g_0..g_8     16-bit codes of S g_i / w_i (p_ref = 0), with S = 2^10 for
 //                  FP16 so pressures and momenta of O(1e-6) stay above the
 //                  FP16 subnormal range; S = 1 for BF16 (FP32 exponent range).
-//   Bytes per node: f 4 + 16, g 18 (92 B read + written per update with phi u).
+//   Layout: the f buffer holds the f_0 plane (N floats) and then 8 planes of
+//   N 32-bit words; word (i - 1, node) packs the codes of f_i (low half) and
+//   g_i (high half), which are pulled from the same neighbour, so one load
+//   serves both and one packed conversion encodes both.  The g buffer holds
+//   the g_0 codes (N 16-bit values).
+//   Bytes per node: 4 + 32 + 2 = 38 per set (92 B read + written per update
+//   with phi u).
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -32,24 +38,11 @@ template <>
 struct Pop<ST_FP32> {
     static size_t f_bytes(size_t N) { return 36 * N; }
     static size_t g_bytes(size_t N) { return 36 * N; }
-    __device__ static float ldf(const void* b, int N, int i, int idx) {
-        return __ldg(static_cast<const float*>(b) + (i * N + idx));
-    }
-    __device__ static float ldg(const void* b, int N, int i, int idx) { return ldf(b, N, i, idx); }
     // store the post-collision set of node idx; f_0 is written as the
     // remainder phi - sum_{i>0} f_i, so the stored populations of a node sum
     // to its phi up to one rounding and sum phi does not drift with the
-    // rounding of the collision
-    __device__ static void stf(void* b, int N, int idx, const float f[9], float phi) {
-#pragma unroll
-        for (int i = 1; i < 9; ++i) static_cast<float*>(b)[i * N + idx] = f[i];
-        static_cast<float*>(b)[idx] = sub(phi, sum8(f));
-    }
-    __device__ static void stg(void* b, int N, int idx, const float g[9]) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) static_cast<float*>(b)[i * N + idx] = g[i];
-    }
-    // both sets, stores of f_i and g_i interleaved (as measured fastest)
+    // rounding of the collision.  Stores of f_i and g_i interleaved (as
+    // measured fastest).
     __device__ static void stfg(void* fb, void* gb, int N, int idx, const float f[9],
                                 const float g[9], float phi) {
         float* F = static_cast<float*>(fb);
@@ -67,17 +60,10 @@ struct Pop<ST_FP32> {
     __device__ static void putf(void* b, int N, int i, int idx, float v) {
         static_cast<float*>(b)[i * N + idx] = v;
     }
-    __device__ static void putg(void* b, int N, int i, int idx, float v) {
+    __device__ static void putg(void*, void* b, int N, int i, int idx, float v) {
         static_cast<float*>(b)[i * N + idx] = v;
     }
     __device__ static float round_f(int, float v) { return v; }
-    // address of entry idx of plane i (for prefetches)
-    __device__ static const void* addr_f(const void* b, int N, int i, int idx) {
-        return static_cast<const float*>(b) + (i * N + idx);
-    }
-    __device__ static const void* addr_g(const void* b, int N, int i, int idx) {
-        return addr_f(b, N, i, idx);
-    }
 };
 
 template <typename H>
@@ -87,6 +73,12 @@ struct Half16<__half> {
     static constexpr float GS = 1024.f;
     __device__ static float to_f(unsigned short u) { return __half2float(__ushort_as_half(u)); }
     __device__ static unsigned short from_f(float v) { return __half_as_ushort(__float2half_rn(v)); }
+    // (from_f(lo), from_f(hi)) in one word, one packed conversion
+    __device__ static unsigned int pack(float lo, float hi) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        return (unsigned int)__half_as_ushort(__low2half(h)) |
+               ((unsigned int)__half_as_ushort(__high2half(h)) << 16);
+    }
 };
 template <>
 struct Half16<__nv_bfloat16> {
@@ -95,19 +87,26 @@ struct Half16<__nv_bfloat16> {
     __device__ static unsigned short from_f(float v) {
         return __bfloat16_as_ushort(__float2bfloat16_rn(v));
     }
+    __device__ static unsigned int pack(float lo, float hi) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return (unsigned int)__bfloat16_as_ushort(__low2bfloat16(h)) |
+               ((unsigned int)__bfloat16_as_ushort(__high2bfloat16(h)) << 16);
+    }
 };
 
 template <typename H>
 struct Shifted16 {
     using C = Half16<H>;
-    static size_t f_bytes(size_t N) { return 4 * N + 16 * N; }
-    static size_t g_bytes(size_t N) { return 18 * N; }
-    __device__ static const unsigned short* fh(const void* b, int N) {
-        return reinterpret_cast<const unsigned short*>(static_cast<const float*>(b) + N);
+    static size_t f_bytes(size_t N) { return 4 * N + 32 * N; }
+    static size_t g_bytes(size_t N) { return 2 * N; }
+    __device__ static const unsigned int* pw(const void* fb, int N) {
+        return reinterpret_cast<const unsigned int*>(static_cast<const float*>(fb) + N);
     }
-    __device__ static unsigned short* fh(void* b, int N) {
-        return reinterpret_cast<unsigned short*>(static_cast<float*>(b) + N);
+    __device__ static unsigned int* pw(void* fb, int N) {
+        return reinterpret_cast<unsigned int*>(static_cast<float*>(fb) + N);
     }
+    __device__ static unsigned short lo(unsigned int w) { return (unsigned short)(w & 0xffffu); }
+    __device__ static unsigned short hi(unsigned int w) { return (unsigned short)(w >> 16); }
     // f_i = w_i (v + 1/2) for i > 0
     __device__ static float dec_f(int i, unsigned short u) {
         return fma_rn(C::to_f(u), w_of(i), 0.5f * w_of(i));
@@ -121,59 +120,39 @@ struct Shifted16 {
     __device__ static unsigned short enc_g(int i, float v) {
         return C::from_f(mul(v, C::GS / w_of(i)));
     }
-    __device__ static float ldf(const void* b, int N, int i, int idx) {
-        if (i == 0) return __ldg(static_cast<const float*>(b) + idx);
-        return dec_f(i, __ldg(fh(b, N) + ((i - 1) * N + idx)));
+    // the word of direction i > 0: the codes enc_f(i, f) | enc_g(i, g) << 16
+    __device__ static unsigned int enc_pair(int i, float f, float g) {
+        return C::pack(fma_rn(f, 1.f / w_of(i), -0.5f), mul(g, C::GS / w_of(i)));
     }
-    __device__ static float ldg(const void* b, int N, int i, int idx) {
-        return dec_g(i, __ldg(static_cast<const unsigned short*>(b) + (i * N + idx)));
-    }
-    // undecoded 16-bit words (f: i > 0), so a pull can issue all its loads
-    // before the first decode waits on one
-    __device__ static unsigned short rawf(const void* b, int N, int i, int idx) {
-        return __ldg(fh(b, N) + ((i - 1) * N + idx));
-    }
-    __device__ static unsigned short rawg(const void* b, int N, int i, int idx) {
-        return __ldg(static_cast<const unsigned short*>(b) + (i * N + idx));
-    }
-    __device__ static void stf(void* b, int N, int idx, const float f[9], float phi) {
+    // store the post-collision set of node idx (f_0 as the remainder)
+    __device__ static void stfg(void* fb, void* gb, int N, int idx, const float f[9],
+                                const float g[9], float phi) {
+        unsigned int* P = pw(fb, N);
         float d[9];
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const unsigned short e = enc_f(i, f[i]);
-            fh(b, N)[(i - 1) * N + idx] = e;
-            d[i] = dec_f(i, e);
+            const unsigned int w = enc_pair(i, f[i], g[i]);
+            P[(i - 1) * N + idx] = w;
+            d[i] = dec_f(i, lo(w));
         }
-        static_cast<float*>(b)[idx] = sub(phi, sum8(d));
+        static_cast<float*>(fb)[idx] = sub(phi, sum8(d));
+        static_cast<unsigned short*>(gb)[idx] = enc_g(0, g[0]);
     }
-    __device__ static void stg(void* b, int N, int idx, const float g[9]) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) static_cast<unsigned short*>(b)[i * N + idx] = enc_g(i, g[i]);
-    }
-    __device__ static void stfg(void* fb, void* gb, int N, int idx, const float f[9],
-                                const float g[9], float phi) {
-        stf(fb, N, idx, f, phi);
-        stg(gb, N, idx, g);
-    }
-    __device__ static void putf(void* b, int N, int i, int idx, float v) {
+    // one entry (checkpoint and initial-state permutations)
+    __device__ static void putf(void* fb, int N, int i, int idx, float v) {
         if (i == 0)
-            static_cast<float*>(b)[idx] = v;
+            static_cast<float*>(fb)[idx] = v;
         else
-            fh(b, N)[(i - 1) * N + idx] = enc_f(i, v);
+            reinterpret_cast<unsigned short*>(pw(fb, N))[2 * ((i - 1) * N + idx)] = enc_f(i, v);
     }
-    __device__ static void putg(void* b, int N, int i, int idx, float v) {
-        static_cast<unsigned short*>(b)[i * N + idx] = enc_g(i, v);
+    __device__ static void putg(void* fb, void* gb, int N, int i, int idx, float v) {
+        if (i == 0)
+            static_cast<unsigned short*>(gb)[idx] = enc_g(0, v);
+        else
+            reinterpret_cast<unsigned short*>(pw(fb, N))[2 * ((i - 1) * N + idx) + 1] = enc_g(i, v);
     }
     // the value a moving population takes after storage
     __device__ static float round_f(int i, float v) { return i == 0 ? v : dec_f(i, enc_f(i, v)); }
-    // address of entry idx of plane i (for prefetches)
-    __device__ static const void* addr_f(const void* b, int N, int i, int idx) {
-        if (i == 0) return static_cast<const float*>(b) + idx;
-        return fh(b, N) + ((i - 1) * N + idx);
-    }
-    __device__ static const void* addr_g(const void* b, int N, int i, int idx) {
-        return static_cast<const unsigned short*>(b) + (i * N + idx);
-    }
 };
 
 template <>
@@ -181,75 +160,79 @@ struct Pop<ST_FP16> : Shifted16<__half> {};
 template <>
 struct Pop<ST_BF16> : Shifted16<__nv_bfloat16> {};
 
-// Pull (stream) the 9 populations of node q through a 16-bit storage format:
-// all nine loads first, then the decodes.  The six wall-dependent loads sit
-// in a branch that is uniform across a warp when the wall flag is a run-time
-// value (BR, the batched kernel: fewer instructions), and are per-lane
-// selects when the kernel is compiled for walls (measured 5% faster there).
-template <int ST, bool F, bool BR>
-__device__ __forceinline__ void pull9_16(const void* s, int N, const Nbr& q, float v[9]) {
+// Pull (stream) node q through a 16-bit storage format: the nine loads first
+// (f_0 and g_0, and one word of (f_i, g_i) codes per moving direction), then
+// the decodes.  The six wall-dependent loads sit in a branch that is uniform
+// across a warp when the wall flag is a run-time value (BR, the batched
+// kernel: fewer instructions), and are per-lane selects when the kernel is
+// compiled for walls (measured 5% faster there).  G: decode g as well.
+template <int ST, bool BR, bool G>
+__device__ __forceinline__ void pull_16(const void* fs, const void* gs, int N, const Nbr& q,
+                                        float f[9], float g[9]) {
     using P = Pop<ST>;
-    auto raw = [&](int i, int idx) { return F ? P::rawf(s, N, i, idx) : P::rawg(s, N, i, idx); };
-    unsigned short u[9];
-    float v0 = 0.f;
-    if (F)
-        v0 = __ldg(static_cast<const float*>(s) + (q.r0 + q.x));
-    else
-        u[0] = raw(0, q.r0 + q.x);
-    u[1] = raw(1, q.r0 + q.xm);
-    u[3] = raw(3, q.r0 + q.xp);
+    const unsigned int* W = P::pw(fs, N);
+    auto raw = [&](int i, int idx) { return __ldg(W + ((i - 1) * N + idx)); };
+    unsigned int w[9];
+    const float f0 = __ldg(static_cast<const float*>(fs) + (q.r0 + q.x));
+    unsigned short g0 = 0;
+    if (G) g0 = __ldg(static_cast<const unsigned short*>(gs) + (q.r0 + q.x));
+    w[1] = raw(1, q.r0 + q.xm);
+    w[3] = raw(3, q.r0 + q.xp);
     if (!BR || q.lo || q.hi) {
-        u[2] = q.lo ? raw(4, q.r0 + q.x) : raw(2, q.rm + q.x);
-        u[4] = q.hi ? raw(2, q.r0 + q.x) : raw(4, q.rp + q.x);
-        u[5] = q.lo ? raw(7, q.r0 + q.x) : raw(5, q.rm + q.xm);
-        u[6] = q.lo ? raw(8, q.r0 + q.x) : raw(6, q.rm + q.xp);
-        u[7] = q.hi ? raw(5, q.r0 + q.x) : raw(7, q.rp + q.xp);
-        u[8] = q.hi ? raw(6, q.r0 + q.x) : raw(8, q.rp + q.xm);
+        w[2] = q.lo ? raw(4, q.r0 + q.x) : raw(2, q.rm + q.x);
+        w[4] = q.hi ? raw(2, q.r0 + q.x) : raw(4, q.rp + q.x);
+        w[5] = q.lo ? raw(7, q.r0 + q.x) : raw(5, q.rm + q.xm);
+        w[6] = q.lo ? raw(8, q.r0 + q.x) : raw(6, q.rm + q.xp);
+        w[7] = q.hi ? raw(5, q.r0 + q.x) : raw(7, q.rp + q.xp);
+        w[8] = q.hi ? raw(6, q.r0 + q.x) : raw(8, q.rp + q.xm);
     } else {
-        u[2] = raw(2, q.rm + q.x);
-        u[4] = raw(4, q.rp + q.x);
-        u[5] = raw(5, q.rm + q.xm);
-        u[6] = raw(6, q.rm + q.xp);
-        u[7] = raw(7, q.rp + q.xp);
-        u[8] = raw(8, q.rp + q.xm);
+        w[2] = raw(2, q.rm + q.x);
+        w[4] = raw(4, q.rp + q.x);
+        w[5] = raw(5, q.rm + q.xm);
+        w[6] = raw(6, q.rm + q.xp);
+        w[7] = raw(7, q.rp + q.xp);
+        w[8] = raw(8, q.rp + q.xm);
     }
     // a bounce-back link decodes with the stored direction's weight: opposite
     // directions share w_i, so the stored and the pulled index agree on it
-    if (F) {
-        v[0] = v0;
+    f[0] = f0;
 #pragma unroll
-        for (int i = 1; i < 9; ++i) v[i] = P::dec_f(i, u[i]);
-    } else {
+    for (int i = 1; i < 9; ++i) f[i] = P::dec_f(i, P::lo(w[i]));
+    if (G) {
+        g[0] = P::dec_g(0, g0);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) v[i] = P::dec_g(i, u[i]);
+        for (int i = 1; i < 9; ++i) g[i] = P::dec_g(i, P::hi(w[i]));
     }
 }
 
-// Pull the 9 populations of node q in any storage format (WALLS as in
+// Pull both population sets of node q in any storage format (WALLS as in
 // make_nbr: < 0 when the wall flag is a run-time value).
 template <int ST, int WALLS = -1>
-__device__ __forceinline__ void pull9f(const void* s, int N, const Nbr& q, float v[9]) {
-    if constexpr (ST == ST_FP32)
-        pull9(static_cast<const float*>(s), (size_t)N, q, v);
-    else
-        pull9_16<ST, true, (WALLS < 0)>(s, N, q, v);
+__device__ __forceinline__ void pull18(const void* fs, const void* gs, int N, const Nbr& q,
+                                       float f[9], float g[9]) {
+    if constexpr (ST == ST_FP32) {
+        pull9(static_cast<const float*>(fs), (size_t)N, q, f);
+        pull9(static_cast<const float*>(gs), (size_t)N, q, g);
+    } else {
+        pull_16<ST, (WALLS < 0), true>(fs, gs, N, q, f, g);
+    }
 }
+// the f set only
 template <int ST, int WALLS = -1>
-__device__ __forceinline__ void pull9g(const void* s, int N, const Nbr& q, float v[9]) {
-    if constexpr (ST == ST_FP32)
-        pull9(static_cast<const float*>(s), (size_t)N, q, v);
-    else
-        pull9_16<ST, false, (WALLS < 0)>(s, N, q, v);
+__device__ __forceinline__ void pull9f(const void* fs, int N, const Nbr& q, float v[9]) {
+    if constexpr (ST == ST_FP32) {
+        pull9(static_cast<const float*>(fs), (size_t)N, q, v);
+    } else {
+        float unused[9];
+        pull_16<ST, (WALLS < 0), false>(fs, nullptr, N, q, v, unused);
+    }
 }
 
 template <int ST, int WALLS = -1>
 __device__ __forceinline__ float phi_at_st(const void* fs, int N, int x, int y, int nx, int ny,
                                            int walls) {
     float v[9];
-    if constexpr (ST == ST_FP32)  // the plain float pull (its address arithmetic measured faster)
-        pull9(static_cast<const float*>(fs), (size_t)N, make_nbr<WALLS>(x, y, nx, ny, walls), v);
-    else
-        pull9f<ST, WALLS>(fs, N, make_nbr<WALLS>(x, y, nx, ny, walls), v);
+    pull9f<ST, WALLS>(fs, N, make_nbr<WALLS>(x, y, nx, ny, walls), v);
     return sum9(v);
 }
 
