@@ -202,8 +202,10 @@ lbm_status lbm_diag_fields_noalloc(const double* d_fields, size_t n, double* d_o
  * addition of this library.
  *
  * lbm_batch_create -- build the batch over ncases handles (1 <= ncases <= 200,
- *   each initialised, none repeated).  The batch keeps a tile table over all
- *   cases and a private stream; handles must outlive the batch.
+ *   each initialised, none repeated, each with at most 65535 x 32767 tiles of
+ *   the smallest tile shape).  The batch owns a case table, device tile
+ *   lists (8 bytes per tile per tile shape and class) and two private
+ *   streams; handles must outlive the batch.
  *   Errors: LBM_ERR_INVALID, LBM_ERR_OOM, LBM_ERR_CUDA (then *out == NULL).
  * lbm_batch_step -- advance every case by nsteps time steps (the same update as
  *   lbm_step, Sec. II, bit for bit).  The cases form two classes, periodic in y

@@ -986,21 +986,15 @@ static_assert(sizeof(BatchTable) <= 32000, "kernel parameters are limited to 32 
 #endif
 
 // One time step of every case of one boundary class (WALLS = 0: periodic in
-// y, 1: walls in y): block t runs tile t of the concatenated tile lists.
+// y, 1: walls in y): block t runs tile t of the class's tile list, whose
+// entry holds (case, tile row << 16 | tile column).
 template <int TX, int TY, int ST, int WALLS>
 __global__ void __launch_bounds__(TX* TY, LBM_BATCH_THREADS / (TX * TY))
-    k_step_batch(const __grid_constant__ BatchTable T, int parity) {
+    k_step_batch(const __grid_constant__ BatchTable T, const int2* __restrict__ tiles, int parity) {
     __shared__ float sphi[TY + 2][TX + 2];
-    const int t = blockIdx.x;
-    int lo = 0, hi = T.ncases - 1;  // the case whose tiles contain block t
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (T.tile0[mid] <= t) lo = mid;
-        else hi = mid - 1;
-    }
-    const CaseDesc& cd = T.c[lo];
-    const int lt = t - T.tile0[lo];
-    const int x0 = (lt % T.tiles_x[lo]) * TX, y0 = (lt / T.tiles_x[lo]) * TY;
+    const int2 e = __ldg(tiles + blockIdx.x);
+    const CaseDesc& cd = T.c[e.x];
+    const int x0 = (e.y & 0xffff) * TX, y0 = (e.y >> 16) * TY;
     const int c = (cd.cur + parity) & 1;
     step_tile<TX, TY, false, WALLS, ST>(sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu,
                                         cd.flag, nullptr, cd.nx, cd.ny, cd.m, x0, y0);
@@ -1015,7 +1009,7 @@ constexpr int BATCH_TY[BATCH_NCAND] = {4, 8, 16, 2, 4};
 constexpr int BATCH_GRAPH_STEPS = 32;  // steps per graph replay (even)
 constexpr int BATCH_TUNE_WARM = 4, BATCH_TUNE_STEPS = 16;
 
-using BatchKernel = void (*)(BatchTable, int);
+using BatchKernel = void (*)(BatchTable, const int2*, int);
 
 template <int ST, int W>
 BatchKernel batch_kernel(int cand) {
@@ -1053,6 +1047,7 @@ struct lbm_batch {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     BatchTable* table = nullptr;  // [class][shape], host side, passed by value
+    int2* d_tiles[BATCH_NCLASS * BATCH_NCAND] = {};  // tile lists on the device, [class][shape]
     int cand[BATCH_NCLASS] = {1, 1};  // tile shape in use per class (index into BATCH_TX/TY)
     bool tuned = false;
     double tuned_us[BATCH_NCLASS][BATCH_NCAND] = {};
@@ -1083,6 +1078,8 @@ static lbm_status bfail(lbm_batch* b, lbm_status st, const char* fmt, ...) {
 static void batch_release(lbm_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     delete[] b->table;
+    for (int2* t : b->d_tiles)
+        if (t) cudaFree(t);
     for (cudaEvent_t e : {b->ev_in, b->ev_out, b->ev_fork, b->ev_join, b->t0, b->t1})
         if (e) cudaEventDestroy(e);
     for (int k = 0; k < BATCH_NCLASS; ++k)
@@ -1112,7 +1109,8 @@ static void batch_sync_table(lbm_batch* b) {
 static lbm_status batch_launch(lbm_batch* b, int cls, int cand, int parity) {
     BatchKernel k = batch_kernel_for(b->storage, cls, cand);
     const BatchTable& T = b->tab(cls, cand);
-    k<<<T.tile0[T.ncases], dim3(BATCH_TX[cand], BATCH_TY[cand]), 0, b->bs[cls]>>>(T, parity);
+    k<<<T.tile0[T.ncases], dim3(BATCH_TX[cand], BATCH_TY[cand]), 0, b->bs[cls]>>>(
+        T, b->d_tiles[cls * BATCH_NCAND + cand], parity);
     LBM_BCUDA(b, cudaGetLastError());
     return LBM_OK;
 }
@@ -1289,6 +1287,27 @@ lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** ou
                 return bad(LBM_ERR_INVALID);
             }
             T.tile0[T.ncases] = (int)tiles;
+            // the tile list: (case, tile row << 16 | tile column), case-major
+            std::vector<int2> list((size_t)tiles);
+            size_t n = 0;
+            for (int j = 0; j < T.ncases; ++j) {
+                const int tx = T.tiles_x[j], ty = (T.c[j].ny + BATCH_TY[k] - 1) / BATCH_TY[k];
+                if (tx > 0xffff || ty > 0x7fff) {
+                    bfail(b, LBM_ERR_INVALID, "a case has more than 65535 x 32767 tiles");
+                    return bad(LBM_ERR_INVALID);
+                }
+                for (int r = 0; r < ty; ++r)
+                    for (int q = 0; q < tx; ++q) list[n++] = make_int2(j, (r << 16) | q);
+            }
+            int2*& d = b->d_tiles[cls * BATCH_NCAND + k];
+            if (tiles > 0) {
+                if (cudaMalloc(&d, tiles * sizeof(int2)) != cudaSuccess ||
+                    cudaMemcpy(d, list.data(), tiles * sizeof(int2), cudaMemcpyHostToDevice) !=
+                        cudaSuccess) {
+                    bfail(b, LBM_ERR_OOM, "tile list allocation failed");
+                    return bad(LBM_ERR_OOM);
+                }
+            }
         }
     for (int c = 0; c < ncases; ++c) b->node_count += (long long)cases[c]->N;
     *out = b;
