@@ -73,6 +73,12 @@ struct Ring {
 #ifndef LBM_PREFETCH_PER10SM
 #define LBM_PREFETCH_PER10SM 15
 #endif
+// prefetch with 16-bit storage too (off: those steps are instruction-bound,
+// and the requests cost more than they hide, 44.5 k -> 43.5 k MLUPS for FP16
+// at 2048^2 with the paired layout)
+#ifndef LBM_PREFETCH_16
+#define LBM_PREFETCH_16 0
+#endif
 // grids with fewer tiles than this many prefetch distances step without it
 #ifndef LBM_PREFETCH_MIN_TILES_X
 #define LBM_PREFETCH_MIN_TILES_X 16
@@ -159,19 +165,20 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 // starts about one resident wave after it, so those DRAM reads are in
 // flight while the current tiles compute: the step is bound by load latency,
 // and a prefetch holds no register and no shared memory.
-template <int TX, int TY>
-__device__ __forceinline__ void prefetch_tile(const float* fs, const float* gs, const float* phiu,
+template <int TX, int TY, int ST>
+__device__ __forceinline__ void prefetch_tile(const void* fs, const void* gs, const float* phiu,
                                               int nx, int ny, int wfold, int bx, int by) {
-    static_assert(18 * (TY + 2) + 2 * TY <= TX * TY, "one request per thread");
+    constexpr int NP = Pop<ST>::PLANES;
+    static_assert(NP * (TY + 2) + 2 * TY <= TX * TY, "one request per thread");
     const int N = nx * ny;
     const int t = threadIdx.y * TX + threadIdx.x;
     const int x0 = bx * TX;
-    if (t < 18 * (TY + 2)) {
+    if (t < NP * (TY + 2)) {
         const int plane = t / (TY + 2), r = t - plane * (TY + 2);
         const int idx = fold_y(by * TY - 1 + r, ny, wfold) * nx + x0;
-        prefetch_l2(plane < 9 ? fs + (plane * N + idx) : gs + ((plane - 9) * N + idx));
-    } else if (t < 18 * (TY + 2) + 2 * TY) {
-        const int k = t - 18 * (TY + 2), yy = by * TY + (k % TY);
+        prefetch_l2(Pop<ST>::plane_addr(fs, gs, N, plane, idx));
+    } else if (t < NP * (TY + 2) + 2 * TY) {
+        const int k = t - NP * (TY + 2), yy = by * TY + (k % TY);
         if (yy < ny) prefetch_l2(phiu + ((k / TY) * N + yy * nx + x0));
     }
 }
@@ -182,15 +189,12 @@ __global__ void __launch_bounds__(TX* TY, LBM_STEP_MINB)
            float* __restrict__ gd, float* __restrict__ phiu, unsigned int* __restrict__ flag,
            double* __restrict__ out, int nx, int ny, Model m, int pf_ahead) {
     __shared__ float sphi[TY + 2][TX + 2];
-    // FP32 storage only: the 16-bit steps are instruction-bound, and there
-    // the prefetch requests cost more than they hide (measured 43.6 k ->
-    // 41.0 k MLUPS at 2048^2 for FP16)
-    if constexpr (!FIELDS && ST == ST_FP32) {
+    if constexpr (!FIELDS && (ST == ST_FP32 || LBM_PREFETCH_16)) {
         if (pf_ahead > 0) {
             const int lin = blockIdx.y * gridDim.x + blockIdx.x + pf_ahead;
             if (lin < gridDim.x * gridDim.y)
-                prefetch_tile<TX, TY>(fs, gs, phiu, nx, ny, WALLS >= 0 ? WALLS : m.walls,
-                                      lin % gridDim.x, lin / gridDim.x);
+                prefetch_tile<TX, TY, ST>(fs, gs, phiu, nx, ny, WALLS >= 0 ? WALLS : m.walls,
+                                          lin % gridDim.x, lin / gridDim.x);
         }
     }
     step_tile<TX, TY, FIELDS, WALLS, ST>(sphi, fs, gs, fd, gd, phiu, flag, out, nx, ny, m,

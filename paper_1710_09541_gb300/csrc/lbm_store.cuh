@@ -64,6 +64,12 @@ struct Pop<ST_FP32> {
         static_cast<float*>(b)[i * N + idx] = v;
     }
     __device__ static float round_f(int, float v) { return v; }
+    // population planes, and the address of entry idx of plane k (prefetches)
+    static constexpr int PLANES = 18;
+    __device__ static const void* plane_addr(const void* fb, const void* gb, int N, int k, int idx) {
+        return k < 9 ? static_cast<const float*>(fb) + (k * N + idx)
+                     : static_cast<const float*>(gb) + ((k - 9) * N + idx);
+    }
 };
 
 template <typename H>
@@ -153,6 +159,13 @@ struct Shifted16 {
     }
     // the value a moving population takes after storage
     __device__ static float round_f(int i, float v) { return i == 0 ? v : dec_f(i, enc_f(i, v)); }
+    // planes: f_0, the 8 word planes, g_0; address of entry idx of plane k
+    static constexpr int PLANES = 10;
+    __device__ static const void* plane_addr(const void* fb, const void* gb, int N, int k, int idx) {
+        if (k == 0) return static_cast<const float*>(fb) + idx;
+        if (k == 9) return static_cast<const unsigned short*>(gb) + idx;
+        return pw(fb, N) + ((k - 1) * N + idx);
+    }
 };
 
 template <>

@@ -99,3 +99,31 @@ def test_batch_rejects_mixed_storage_and_repeats(lbm):
     finally:
         a.close()
         b.close()
+
+
+def test_batch_at_the_case_limit(lbm):
+    """200 small cases (the kernel-parameter table's capacity) of mixed
+    boundary kinds and sizes; a 201st is rejected."""
+    specs = []
+    r = np.random.default_rng(4)
+    for k in range(201):
+        nx, ny = int(r.integers(8, 40)), int(r.integers(4, 24))
+        P = dict(cases.params_static_drop(ratio=10.0), bc_y=k % 3)
+        phi0 = cases.drop(nx, ny, min(nx, ny) / 3, 3.0, walls_y=k % 3 > 0)
+        specs.append(dict(nx=nx, ny=ny, params=P, phi0=phi0, ux0=None, uy0=None))
+    A = _lattices(lbm, specs[:200], 1)
+    B = _lattices(lbm, specs[:200], 1)
+    extra = _lattices(lbm, specs[200:], 1)
+    try:
+        with pytest.raises(lbm.LbmError):
+            lbm.Batch(A + extra)
+        with lbm.Batch(A) as bt:
+            bt.step(133)
+        for lat in B:
+            lat.step(133)
+        for a, b in zip(A, B):
+            for x, y in zip(a.get_state(), b.get_state()):
+                assert np.array_equal(x, y)
+    finally:
+        for lat in A + B + extra:
+            lat.close()
