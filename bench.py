@@ -205,6 +205,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings over all ranks (every rank gets
+    it); dist is torch.distributed or None for a single process."""
+    import torch
+
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_mlups(nodes_per_rank, steps, world, seconds):
+    """Aggregate MLUPS of N replicas, each advancing nodes_per_rank nodes by
+    `steps` steps, timed by the slowest rank (weak scaling)."""
+    return world * nodes_per_rank * steps / seconds / 1e6
+
+
 STORAGE_NAMES = {0: "fp32", 1: "fp16_shifted", 2: "bf16_shifted"}
 # FP16/BF16 shifted storage: f_0 FP32 (4 B) + f_1..8 and g_0..8 16-bit (34 B)
 # per set, read and written, plus (phi u): 2 * 38 + 16
@@ -358,14 +375,11 @@ def run_ours(args):
         batched = run_batched(torch, lbm, stream, args.batch_steps)
         storage_variants = run_storage_variants(torch, lbm, stream, 2000)
 
-    times = torch.tensor([ms / 1e3, e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    t_dev, t_e2e = times.tolist()
+    t_dev, t_e2e = max_over_ranks([ms / 1e3, e2e_s], dist, "cuda")
 
     if rank == 0:
-        value = world * N * args.steps / t_dev / 1e6
-        e2e_value = world * N * args.steps / t_e2e / 1e6
+        value = whole_job_mlups(N, args.steps, world, t_dev)
+        e2e_value = whole_job_mlups(N, args.steps, world, t_e2e)
         ms_step = t_dev * 1e3 / args.steps
         peak, peak_kind = _peaks()
         achieved = BYTES_PER_LU * N / (ms_step * 1e-3) / 1e9

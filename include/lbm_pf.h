@@ -217,7 +217,11 @@ lbm_status lbm_diag_fields_noalloc(const double* d_fields, size_t n, double* d_o
  *   for each class on its own first 100 steps and keeps the fastest.
  *   Ordered after earlier work on the cases' stream, and later work on that
  *   stream waits for it.  A case may also be stepped on its own between batch
- *   steps.
+ *   steps.  If any case was created with check_every > 0, the call ends by
+ *   synchronising and returns LBM_ERR_NONFINITE (the first such case named by
+ *   lbm_batch_last_error) when a case with check_every > 0 produced a
+ *   non-finite phi, u or p during the call; all cases' flags are cleared.
+ *   Otherwise the call is asynchronous.
  * lbm_batch_info -- for class cls (0: periodic cases, 1: walled cases): the
  *   number of cases, the tile shape in use, its measured microseconds per
  *   step (0 before tuning or for an empty class) and whether tuning ran; any

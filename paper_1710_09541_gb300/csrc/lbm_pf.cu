@@ -1037,6 +1037,17 @@ BatchKernel batch_kernel_for(int storage, int cls, int cand) {
     return batch_kernel_st<ST_FP32>(cls, cand);
 }
 
+// Copy the non-finite flags of one class's cases to out[slot[j]] and clear
+// them (one thread per case).
+__global__ void k_batch_flags(const __grid_constant__ BatchTable T, const int* __restrict__ slot,
+                              unsigned int* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= T.ncases) return;
+    unsigned int* f = T.c[j].flag;
+    out[slot[j]] = *f;
+    *f = 0u;
+}
+
 }  // namespace
 
 struct lbm_batch {
@@ -1052,6 +1063,9 @@ struct lbm_batch {
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     BatchTable* table = nullptr;  // [class][shape], host side, passed by value
     int2* d_tiles[BATCH_NCLASS * BATCH_NCAND] = {};  // tile lists on the device, [class][shape]
+    bool check = false;                 // some case asks for non-finite checks (check_every > 0)
+    int* d_slot[BATCH_NCLASS] = {};     // per class: the batch index of each class slot
+    unsigned int* d_flags = nullptr;    // gathered flags, one per case
     int cand[BATCH_NCLASS] = {1, 1};  // tile shape in use per class (index into BATCH_TX/TY)
     bool tuned = false;
     double tuned_us[BATCH_NCLASS][BATCH_NCAND] = {};
@@ -1084,6 +1098,9 @@ static void batch_release(lbm_batch* b) {
     delete[] b->table;
     for (int2* t : b->d_tiles)
         if (t) cudaFree(t);
+    for (int* t : b->d_slot)
+        if (t) cudaFree(t);
+    if (b->d_flags) cudaFree(b->d_flags);
     for (cudaEvent_t e : {b->ev_in, b->ev_out, b->ev_fork, b->ev_join, b->t0, b->t1})
         if (e) cudaEventDestroy(e);
     for (int k = 0; k < BATCH_NCLASS; ++k)
@@ -1313,7 +1330,27 @@ lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** ou
                 }
             }
         }
-    for (int c = 0; c < ncases; ++c) b->node_count += (long long)cases[c]->N;
+    for (int c = 0; c < ncases; ++c) {
+        b->node_count += (long long)cases[c]->N;
+        if (cases[c]->prm.check_every > 0) b->check = true;
+    }
+    // batch index of each class slot, for gathering the cases' flags
+    for (int cls = 0; cls < BATCH_NCLASS; ++cls) {
+        if (!b->ncls[cls]) continue;
+        std::vector<int> idx;
+        for (int c = 0; c < ncases; ++c)
+            if (b->cls_of[c] == cls) idx.push_back(c);
+        if (cudaMalloc(&b->d_slot[cls], idx.size() * sizeof(int)) != cudaSuccess ||
+            cudaMemcpy(b->d_slot[cls], idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+            bfail(b, LBM_ERR_OOM, "slot table allocation failed");
+            return bad(LBM_ERR_OOM);
+        }
+    }
+    if (cudaMalloc(&b->d_flags, ncases * sizeof(unsigned int)) != cudaSuccess) {
+        bfail(b, LBM_ERR_OOM, "flag array allocation failed");
+        return bad(LBM_ERR_OOM);
+    }
     *out = b;
     return LBM_OK;
 }
@@ -1377,6 +1414,28 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
     // cases' current buffers (and with them the tables) follow
     batch_flip(b, nsteps);
     batch_sync_table(b);
+    if (b->check) {
+        // the cases' non-finite flags (set by any step of this call), gathered
+        // and cleared on the device, then read on the host
+        for (int cls = 0; cls < BATCH_NCLASS; ++cls)
+            if (b->ncls[cls]) {
+                const BatchTable& T = b->tab(cls, 0);
+                k_batch_flags<<<(T.ncases + 127) / 128, 128, 0, b->bs[0]>>>(T, b->d_slot[cls],
+                                                                            b->d_flags);
+                LBM_BCUDA(b, cudaGetLastError());
+            }
+        std::vector<unsigned int> fl(b->ncases);
+        LBM_BCUDA(b, cudaMemcpyAsync(fl.data(), b->d_flags, b->ncases * sizeof(unsigned int),
+                                     cudaMemcpyDeviceToHost, b->bs[0]));
+        LBM_BCUDA(b, cudaStreamSynchronize(b->bs[0]));
+        for (int c = 0; c < b->ncases; ++c)
+            if (fl[c] && b->cases[c]->prm.check_every > 0) {
+                LBM_BCUDA(b, cudaEventRecord(b->ev_out, b->bs[0]));
+                LBM_BCUDA(b, cudaStreamWaitEvent(b->user, b->ev_out, 0));
+                return bfail(b, LBM_ERR_NONFINITE,
+                             "case %d produced a non-finite phi, u or p in this batch step", c);
+            }
+    }
     LBM_BCUDA(b, cudaEventRecord(b->ev_out, b->bs[0]));
     LBM_BCUDA(b, cudaStreamWaitEvent(b->user, b->ev_out, 0));
     return LBM_OK;

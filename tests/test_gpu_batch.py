@@ -127,3 +127,29 @@ def test_batch_at_the_case_limit(lbm):
     finally:
         for lat in A + B + extra:
             lat.close()
+
+
+def test_batch_reports_nonfinite_case(lbm):
+    """A NaN planted in one case's state (host side, through lbm_set_state)
+    makes a batch step with check_every > 0 fail with LBM_ERR_NONFINITE naming
+    that case; the flags are cleared afterwards."""
+    specs = cases.batch_cases(n=4, seed=21)
+    for sp in specs:
+        sp["params"] = dict(sp["params"], check_every=1)
+    A = _lattices(lbm, specs, 0)
+    try:
+        with lbm.Batch(A) as bt:
+            bt.step(3)
+            f, g, phiu = A[2].get_state()
+            f = f.copy()
+            f[3, 10, 10] = np.nan
+            A[2].set_state(f, g, phiu)
+            with pytest.raises(lbm.LbmError) as e:
+                bt.step(4)
+            assert e.value.status == lbm.LBM_ERR_NONFINITE
+            assert "case 2" in str(e.value)
+            for k in (0, 1, 3):
+                assert np.isfinite(A[k].diag()[0])
+    finally:
+        for lat in A:
+            lat.close()
