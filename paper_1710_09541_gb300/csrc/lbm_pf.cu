@@ -58,10 +58,10 @@ struct Ring {
 #define LBM_STEP_TX 32
 #endif
 #ifndef LBM_STEP_TY
-#define LBM_STEP_TY 8
+#define LBM_STEP_TY 4
 #endif
 #ifndef LBM_STEP_MINB
-#define LBM_STEP_MINB 4
+#define LBM_STEP_MINB 8
 #endif
 // load (phi u) of the previous step with the node's pulls instead of just
 // before the collision
@@ -69,9 +69,10 @@ struct Ring {
 #define LBM_EARLY_PHIU 1
 #endif
 // L2 prefetch distance of the step kernel in tiles, per 10 SMs (0: off);
-// 15 = 1.5 tiles per SM, about a third of a resident wave at 4 blocks/SM
+// 30 = 3 tiles of 32 x 4 per SM, about a third of a resident wave at 8
+// blocks/SM (measured best of 20 / 30 / 40 / 60)
 #ifndef LBM_PREFETCH_PER10SM
-#define LBM_PREFETCH_PER10SM 15
+#define LBM_PREFETCH_PER10SM 30
 #endif
 // prefetch with 16-bit storage too (off: those steps are instruction-bound,
 // and the requests cost more than they hide, 44.5 k -> 43.5 k MLUPS for FP16
