@@ -111,6 +111,26 @@ typedef struct {
 lbm_status lbm_create(int nx, int ny, const lbm_params* p, lbm_handle** out);
 
 /*
+ * Handles whose device memory belongs to the caller (for example a PyTorch
+ * tensor, so that the framework's caching allocator owns and accounts for
+ * it).  The same state as lbm_create describes, laid out in one buffer.
+ *
+ * lbm_workspace_bytes -- validate the parameters as lbm_create does and write
+ *   to *bytes the size of the device workspace an nx x ny handle needs.  Makes
+ *   no CUDA call.  Errors: LBM_ERR_INVALID.
+ * lbm_create_in -- create a handle whose device buffers are carved from
+ *   d_workspace: device (or managed) memory of the current device, 256-byte
+ *   aligned, at least lbm_workspace_bytes long.  The handle never frees it;
+ *   the caller keeps it alive, and untouched by other work, until
+ *   lbm_destroy.  Otherwise the handle behaves exactly as one from lbm_create.
+ *   Errors: LBM_ERR_INVALID (bad parameters, NULL, too small, misaligned, or
+ *   not device memory of the current device), LBM_ERR_CUDA.
+ */
+lbm_status lbm_workspace_bytes(int nx, int ny, const lbm_params* p, size_t* bytes);
+lbm_status lbm_create_in(int nx, int ny, const lbm_params* p, void* d_workspace, size_t bytes,
+                         lbm_handle** out);
+
+/*
  * lbm_init -- set the state to equilibrium: f_i = f_i^eq(phi0, u0) (Eq. 9),
  * g_i = g_i^eq(p0, rho(phi0), u0) (Eqs. 13, 16, 17), and the previous-step
  * (phi u) to phi0 * u0.  phi0 is required; ux0, uy0, p0 may be NULL (= 0).

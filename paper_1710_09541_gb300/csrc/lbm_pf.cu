@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -435,6 +436,7 @@ struct lbm_handle {
     // TMA-staged step kernel (used when kernel != LBM_KERNEL_GENERIC and nx % 4 == 0)
     bool use_tma = false;
     int pf_ahead = 0;  // L2 prefetch distance of the step kernel, in tiles
+    bool owns_memory = true;  // false: the device buffers live in a caller's workspace
     CUtensorMap tm_f[2], tm_g[2], tm_u;
     int tiles_x = 0, ntiles = 0, tma_grid = 0;
     char err[512] = {0};
@@ -519,6 +521,7 @@ static Model make_model(const lbm_params& p) {
 }
 
 static void release(lbm_handle* h) {
+    if (!h->owns_memory) return;  // a caller's workspace stays the caller's
     for (int b = 0; b < 2; ++b) {
         cudaFree(h->f[b]);
         cudaFree(h->g[b]);
@@ -528,6 +531,39 @@ static void release(lbm_handle* h) {
     cudaFree(h->red_part);
     cudaFree(h->red_res);
     cudaFree(h->flag);
+}
+
+static size_t f_bytes(int storage, size_t N) {
+    return storage == LBM_STORE_FP32 ? Pop<ST_FP32>::f_bytes(N) : Pop<ST_FP16>::f_bytes(N);
+}
+static size_t g_bytes(int storage, size_t N) {
+    return storage == LBM_STORE_FP32 ? Pop<ST_FP32>::g_bytes(N) : Pop<ST_FP16>::g_bytes(N);
+}
+
+// The device buffers of one handle, in workspace order, each starting on a
+// 256-byte boundary: f[0], f[1], g[0], g[1], phi u, staging, block partials,
+// results, flag.
+struct Layout {
+    size_t size[9];
+    size_t offset[9];
+    size_t total;
+};
+static Layout layout_of(int nx, int ny, int storage) {
+    const size_t N = (size_t)nx * ny;
+    const size_t fpop = f_bytes(storage, N), gpop = g_bytes(storage, N);
+    const size_t staging = (20 * N * sizeof(float) > 5 * N * sizeof(double)) ? 20 * N * sizeof(float)
+                                                                              : 5 * N * sizeof(double);
+    Layout L{{fpop, fpop, gpop, gpop, 2 * N * sizeof(float), staging, 4 * RED_BLOCKS * sizeof(double),
+              4 * sizeof(double), sizeof(unsigned int)},
+             {},
+             0};
+    size_t at = 0;
+    for (int k = 0; k < 9; ++k) {
+        L.offset[k] = at;
+        at += (L.size[k] + 255) / 256 * 256;
+    }
+    L.total = at;
+    return L;
 }
 
 static int grid1d(size_t N) {
@@ -577,13 +613,6 @@ static lbm_status launch_step(lbm_handle* h, bool fields, double* out) {
     LBM_CUDA(h, cudaGetLastError());
     if (!fields) h->cur ^= 1;
     return LBM_OK;
-}
-
-static size_t f_bytes(int storage, size_t N) {
-    return storage == LBM_STORE_FP32 ? Pop<ST_FP32>::f_bytes(N) : Pop<ST_FP16>::f_bytes(N);
-}
-static size_t g_bytes(int storage, size_t N) {
-    return storage == LBM_STORE_FP32 ? Pop<ST_FP32>::g_bytes(N) : Pop<ST_FP16>::g_bytes(N);
 }
 
 static lbm_status check_flag(lbm_handle* h) {
@@ -651,15 +680,9 @@ static lbm_status setup_tma(lbm_handle* h) {
 
 extern "C" {
 
-lbm_status lbm_create(int nx, int ny, const lbm_params* p, lbm_handle** out) {
-    if (!out) return LBM_ERR_INVALID;
-    *out = nullptr;
-    char msg[256];
-    lbm_status st = validate(nx, ny, p, msg, sizeof msg);
-    if (st != LBM_OK) {
-        fprintf(stderr, "lbm_create: %s\n", msg);
-        return st;
-    }
+// Shared by lbm_create (ws == NULL: the handle allocates its buffers) and
+// lbm_create_in (the buffers are carved from the caller's workspace ws).
+static lbm_status create_handle(int nx, int ny, const lbm_params* p, void* ws, lbm_handle** out) {
     lbm_handle* h = new (std::nothrow) lbm_handle();
     if (!h) return LBM_ERR_OOM;
     h->nx = nx;
@@ -668,20 +691,18 @@ lbm_status lbm_create(int nx, int ny, const lbm_params* p, lbm_handle** out) {
     h->prm = *p;
     h->model = make_model(*p);
     h->stream = (cudaStream_t)p->stream;
+    h->owns_memory = ws == nullptr;
     cudaError_t e = cudaGetDevice(&h->device);
-    const size_t fpop = f_bytes(p->storage, h->N), gpop = g_bytes(p->storage, h->N);
-    const size_t staging = (20 * h->N * sizeof(float) > 5 * h->N * sizeof(double))
-                               ? 20 * h->N * sizeof(float)
-                               : 5 * h->N * sizeof(double);
-    if (e == cudaSuccess) e = cudaMalloc(&h->f[0], fpop);
-    if (e == cudaSuccess) e = cudaMalloc(&h->f[1], fpop);
-    if (e == cudaSuccess) e = cudaMalloc(&h->g[0], gpop);
-    if (e == cudaSuccess) e = cudaMalloc(&h->g[1], gpop);
-    if (e == cudaSuccess) e = cudaMalloc(&h->phiu, 2 * h->N * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&h->staging, staging);
-    if (e == cudaSuccess) e = cudaMalloc(&h->red_part, 4 * RED_BLOCKS * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&h->red_res, 4 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&h->flag, sizeof(unsigned int));
+    const Layout L = layout_of(nx, ny, p->storage);
+    void** slot[9] = {(void**)&h->f[0], (void**)&h->f[1], (void**)&h->g[0], (void**)&h->g[1],
+                      (void**)&h->phiu, &h->staging,      (void**)&h->red_part, (void**)&h->red_res,
+                      (void**)&h->flag};
+    for (int k = 0; k < 9 && e == cudaSuccess; ++k) {
+        if (ws)
+            *slot[k] = static_cast<char*>(ws) + L.offset[k];
+        else
+            e = cudaMalloc(slot[k], L.size[k]);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     int sms = 0;
@@ -713,6 +734,60 @@ lbm_status lbm_create(int nx, int ny, const lbm_params* p, lbm_handle** out) {
     }
     *out = h;
     return LBM_OK;
+}
+
+lbm_status lbm_create(int nx, int ny, const lbm_params* p, lbm_handle** out) {
+    if (!out) return LBM_ERR_INVALID;
+    *out = nullptr;
+    char msg[256];
+    lbm_status st = validate(nx, ny, p, msg, sizeof msg);
+    if (st != LBM_OK) {
+        fprintf(stderr, "lbm_create: %s\n", msg);
+        return st;
+    }
+    return create_handle(nx, ny, p, nullptr, out);
+}
+
+lbm_status lbm_workspace_bytes(int nx, int ny, const lbm_params* p, size_t* bytes) {
+    if (!bytes) return LBM_ERR_INVALID;
+    *bytes = 0;
+    char msg[256];
+    lbm_status st = validate(nx, ny, p, msg, sizeof msg);
+    if (st != LBM_OK) {
+        fprintf(stderr, "lbm_workspace_bytes: %s\n", msg);
+        return st;
+    }
+    *bytes = layout_of(nx, ny, p->storage).total;
+    return LBM_OK;
+}
+
+lbm_status lbm_create_in(int nx, int ny, const lbm_params* p, void* d_workspace, size_t bytes,
+                         lbm_handle** out) {
+    if (!out) return LBM_ERR_INVALID;
+    *out = nullptr;
+    char msg[256];
+    lbm_status st = validate(nx, ny, p, msg, sizeof msg);
+    if (st != LBM_OK) {
+        fprintf(stderr, "lbm_create_in: %s\n", msg);
+        return st;
+    }
+    const size_t need = layout_of(nx, ny, p->storage).total;
+    if (!d_workspace || bytes < need || ((uintptr_t)d_workspace % 256) != 0) {
+        fprintf(stderr, "lbm_create_in: need a 256-byte aligned device workspace of at least %zu "
+                        "bytes, got %p and %zu bytes\n", need, d_workspace, bytes);
+        return LBM_ERR_INVALID;
+    }
+    // the workspace must be device (or managed) memory of the current device:
+    // a host pointer here would make every kernel fault
+    cudaPointerAttributes at{};
+    int dev = -1;
+    if (cudaPointerGetAttributes(&at, d_workspace) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev) {
+        cudaGetLastError();
+        fprintf(stderr, "lbm_create_in: the workspace is not device memory of the current device\n");
+        return LBM_ERR_INVALID;
+    }
+    return create_handle(nx, ny, p, d_workspace, out);
 }
 
 void lbm_destroy(lbm_handle* h) {

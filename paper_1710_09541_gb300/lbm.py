@@ -33,7 +33,7 @@ EXPORTS = ("lbm_create", "lbm_init", "lbm_step", "lbm_get_fields", "lbm_state_by
            "lbm_get_state", "lbm_set_state", "lbm_diag", "lbm_synchronize", "lbm_destroy",
            "lbm_last_error", "lbm_diag_fields_noalloc", "lbm_batch_create", "lbm_batch_step",
            "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error",
-           "lbm_spreading_radius", "lbm_probe")
+           "lbm_spreading_radius", "lbm_probe", "lbm_workspace_bytes", "lbm_create_in")
 
 
 class LbmError(RuntimeError):
@@ -86,6 +86,8 @@ def load() -> ctypes.CDLL:
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_diag_fields_noalloc.argtypes = [vp, sz, vp, vp, ctypes.c_char_p, sz]
     L.lbm_spreading_radius.argtypes = [vp, i, i, pd, pd]
+    L.lbm_workspace_bytes.argtypes = [i, i, ctypes.POINTER(lbm_params), ctypes.POINTER(sz)]
+    L.lbm_create_in.argtypes = [i, i, ctypes.POINTER(lbm_params), vp, sz, ctypes.POINTER(vp)]
     pi = ctypes.POINTER(ctypes.c_int)
     L.lbm_probe.argtypes = [vp, i, pi, pi, pd, pd, pd, pd, pd]
     L.lbm_diag_fields_noalloc.restype = ctypes.c_int
@@ -140,17 +142,40 @@ def _dptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-class Lattice:
-    """One lattice on the current CUDA device: ``Lattice(nx, ny, **params)``."""
+def workspace_bytes(nx: int, ny: int, **params) -> int:
+    """lbm_workspace_bytes: device bytes an nx x ny lattice needs."""
+    L = load()
+    p = make_params(**params)
+    n = ctypes.c_size_t()
+    rc = L.lbm_workspace_bytes(int(nx), int(ny), ctypes.byref(p), ctypes.byref(n))
+    if rc != LBM_OK:
+        raise LbmError(rc, "lbm_workspace_bytes failed (see stderr)")
+    return n.value
 
-    def __init__(self, nx: int, ny: int, stream=None, **params):
+
+class Lattice:
+    """One lattice on the current CUDA device: ``Lattice(nx, ny, **params)``.
+
+    With ``workspace`` (a contiguous CUDA tensor of at least
+    ``workspace_bytes(nx, ny, **params)`` bytes) the device state lives in that
+    tensor (lbm_create_in); the lattice keeps a reference to it."""
+
+    def __init__(self, nx: int, ny: int, stream=None, workspace=None, **params):
         self._L = load()
         self.nx, self.ny = int(nx), int(ny)
         self.params = make_params(stream=stream, **params)
         h = ctypes.c_void_p()
-        rc = self._L.lbm_create(self.nx, self.ny, ctypes.byref(self.params), ctypes.byref(h))
+        if workspace is None:
+            rc = self._L.lbm_create(self.nx, self.ny, ctypes.byref(self.params), ctypes.byref(h))
+        else:
+            if not workspace.is_contiguous():
+                raise ValueError("workspace must be contiguous")
+            nbytes = workspace.numel() * workspace.element_size()
+            rc = self._L.lbm_create_in(self.nx, self.ny, ctypes.byref(self.params),
+                                       workspace.data_ptr(), nbytes, ctypes.byref(h))
         if rc != LBM_OK:
             raise LbmError(rc, "lbm_create failed (see stderr)")
+        self._workspace = workspace
         self._h = h
 
     # -- helpers -------------------------------------------------------------

@@ -75,6 +75,29 @@ def test_create_rejects_bad_sizes(L, nx, ny):
     assert L.lbm_create(nx, ny, ctypes.byref(p), ctypes.byref(h)) == lbm.LBM_ERR_INVALID
 
 
+def test_workspace_bytes_and_create_in_checks(L):
+    """No CUDA call is needed to size a workspace or to reject a bad one."""
+    p = lbm.make_params(storage=lbm.LBM_STORE_FP16_SHIFTED)
+    n = ctypes.c_size_t()
+    assert L.lbm_workspace_bytes(64, 32, ctypes.byref(p), ctypes.byref(n)) == lbm.LBM_OK
+    N = 64 * 32
+    assert n.value >= 2 * 38 * N + 8 * N + 80 * N and n.value % 256 == 0
+    p32 = lbm.make_params()
+    n32 = ctypes.c_size_t()
+    assert L.lbm_workspace_bytes(64, 32, ctypes.byref(p32), ctypes.byref(n32)) == lbm.LBM_OK
+    assert n32.value > n.value                        # FP32 populations take 160 B/node
+    bad = lbm.make_params(tau_h=0.4)
+    assert L.lbm_workspace_bytes(64, 32, ctypes.byref(bad), ctypes.byref(n)) == lbm.LBM_ERR_INVALID
+    h = ctypes.c_void_p()
+    # NULL, too small, misaligned: rejected before the pointer is ever used
+    assert L.lbm_create_in(64, 32, ctypes.byref(p32), None, n32.value, ctypes.byref(h)) == lbm.LBM_ERR_INVALID
+    assert L.lbm_create_in(64, 32, ctypes.byref(p32), 1 << 20, n32.value - 1,
+                           ctypes.byref(h)) == lbm.LBM_ERR_INVALID
+    assert L.lbm_create_in(64, 32, ctypes.byref(p32), (1 << 20) + 16, n32.value,
+                           ctypes.byref(h)) == lbm.LBM_ERR_INVALID
+    assert not h.value
+
+
 def test_open_top_needs_two_rows(L):
     p = lbm.make_params(bc_y=lbm.LBM_BC_WALL_OPEN)
     h = ctypes.c_void_p()
