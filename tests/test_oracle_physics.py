@@ -174,7 +174,8 @@ def test_single_phase_poiseuille():
     y = np.arange(ny) + 0.5
     exact = 1e-6 * y * (ny - y) / (2 * 0.1)
     u = _poiseuille(ny, nx, P, 20000, np.zeros(ny))
-    assert np.sqrt(((u - exact) ** 2).sum() / (exact ** 2).sum()) < 2e-3
+    # measured 7.0e-4 (L2): the half-way wall's O(1/ny^2) placement error
+    assert np.sqrt(((u - exact) ** 2).sum() / (exact ** 2).sum()) < 1e-3
 
 
 def test_open_top_half_poiseuille_first_order():
