@@ -275,6 +275,14 @@ def run_batched(torch, lbm, stream, steps, storage=1):
     b.close()
     for lat in bat:
         lat.close()
+    # the same batch with FP32 storage: batching alone, at the plain path's precision
+    bat32 = make(0)
+    b32 = lbm.Batch(bat32)
+    b32.step(100)
+    t_b32 = _time_steps(torch, stream, lambda: b32.step(steps))
+    b32.close()
+    for lat in bat32:
+        lat.close()
     drops = [k for k, sp in enumerate(specs) if sp["kind"] == "static_drop"]
     v_bat = nodes * steps / t_bat / 1e6
     v_seq = nodes * steps / t_seq / 1e6
@@ -284,6 +292,7 @@ def run_batched(torch, lbm, stream, steps, storage=1):
         "cases": len(specs), "nodes": nodes, "steps_per_case": steps + 5,
         "storage": STORAGE_NAMES[storage], "value": v_bat, "unit": UNIT,
         "sequential_fp32": v_seq, "speedup_vs_sequential_fp32": v_bat / v_seq,
+        "batched_fp32": nodes * steps / t_b32 / 1e6,
         "tile": {k: list(info[k]["tile"]) for k in ("periodic", "walls")},
         "tuned_us_per_step": {k: info[k]["us"] for k in ("periodic", "walls")},
         "bytes_per_lu": bpl,

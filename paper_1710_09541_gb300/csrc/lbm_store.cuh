@@ -27,6 +27,14 @@
 
 #include "lbm_kernels.cuh"
 
+// 16-bit pulls of kernels compiled for walls: per-lane selects (0) or the
+// warp-uniform branch the run-time-wall kernels use (1).  With 32 x 8 tiles
+// the selects were 5% faster; with the 32 x 4 tiles the branch is (walled
+// impact 2400 x 600, FP16: 39.1 k -> 40.1-41.0 k MLUPS).
+#ifndef LBM_WALL_BRANCH
+#define LBM_WALL_BRANCH 1
+#endif
+
 namespace lbmpf {
 
 enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2 };
@@ -176,9 +184,8 @@ struct Pop<ST_BF16> : Shifted16<__nv_bfloat16> {};
 // Pull (stream) node q through a 16-bit storage format: the nine loads first
 // (f_0 and g_0, and one word of (f_i, g_i) codes per moving direction), then
 // the decodes.  The six wall-dependent loads sit in a branch that is uniform
-// across a warp when the wall flag is a run-time value (BR, the batched
-// kernel: fewer instructions), and are per-lane selects when the kernel is
-// compiled for walls (measured 5% faster there).  G: decode g as well.
+// across a warp (BR; a warp covers part of one tile row), or are per-lane
+// selects.  G: decode g as well.
 template <int ST, bool BR, bool G>
 __device__ __forceinline__ void pull_16(const void* fs, const void* gs, int N, const Nbr& q,
                                         float f[9], float g[9]) {
@@ -227,7 +234,7 @@ __device__ __forceinline__ void pull18(const void* fs, const void* gs, int N, co
         pull9(static_cast<const float*>(fs), (size_t)N, q, f);
         pull9(static_cast<const float*>(gs), (size_t)N, q, g);
     } else {
-        pull_16<ST, (WALLS < 0), true>(fs, gs, N, q, f, g);
+        pull_16<ST, (WALLS < 0) || LBM_WALL_BRANCH, true>(fs, gs, N, q, f, g);
     }
 }
 // the f set only
@@ -237,7 +244,7 @@ __device__ __forceinline__ void pull9f(const void* fs, int N, const Nbr& q, floa
         pull9(static_cast<const float*>(fs), (size_t)N, q, v);
     } else {
         float unused[9];
-        pull_16<ST, (WALLS < 0), false>(fs, nullptr, N, q, v, unused);
+        pull_16<ST, (WALLS < 0) || LBM_WALL_BRANCH, false>(fs, nullptr, N, q, v, unused);
     }
 }
 
