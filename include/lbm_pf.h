@@ -75,7 +75,7 @@ enum {
 /* step kernel (kernel); both compute the same arithmetic */
 enum {
     LBM_KERNEL_AUTO = 0,    /* the faster on GB300: currently LBM_KERNEL_GENERIC */
-    LBM_KERNEL_GENERIC = 1, /* 32 x 8 tiles, one thread per node, direct loads; any grid */
+    LBM_KERNEL_GENERIC = 1, /* 32 x 4 tiles, one thread per node, direct loads; any grid */
     LBM_KERNEL_TMA = 2      /* persistent, tiles staged by bulk tensor copies; nx % 4 == 0,
                                nx >= 72, ny >= 20 */
 };

@@ -86,7 +86,7 @@ struct Ring {
 #define LBM_PREFETCH_MIN_TILES_X 16
 #endif
 // One TX x TY tile with origin (x0, y0): the body shared by the single-case
-// step kernel and the batched persistent kernel (so both give the same bits).
+// step kernel and the batched kernel (so both give the same bits).
 template <int TX, int TY, bool FIELDS, int WALLS, int ST>
 __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __restrict__ fs,
                                           const float* __restrict__ gs, float* __restrict__ fd,
@@ -164,7 +164,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 // Ask L2 for the rows tile (bx, by) will pull: rows by*TY - 1 .. by*TY + TY
 // of the 18 population planes and the TY rows of (phi u), from column bx*TX
 // (one request per row and plane).  Called by a block for the tile that
-// starts about one resident wave after it, so those DRAM reads are in
+// starts about a third of a resident wave after it, so those DRAM reads are in
 // flight while the current tiles compute: the step is bound by load latency,
 // and a prefetch holds no register and no shared memory.
 template <int TX, int TY, int ST>
