@@ -62,7 +62,7 @@ struct Ring {
 #define LBM_STEP_TY 4
 #endif
 #ifndef LBM_STEP_MINB
-#define LBM_STEP_MINB 8
+#define LBM_STEP_MINB 0
 #endif
 // load (phi u) of the previous step with the node's pulls instead of just
 // before the collision
@@ -80,6 +80,10 @@ struct Ring {
 // at 2048^2 with the paired layout)
 #ifndef LBM_PREFETCH_16
 #define LBM_PREFETCH_16 0
+#endif
+// also prefetch the tile two distances ahead
+#ifndef LBM_PREFETCH_TWICE
+#define LBM_PREFETCH_TWICE 0
 #endif
 // grids with fewer tiles than this many prefetch distances step without it
 #ifndef LBM_PREFETCH_MIN_TILES_X
@@ -185,8 +189,22 @@ __device__ __forceinline__ void prefetch_tile(const void* fs, const void* gs, co
     }
 }
 
+// Resident blocks per SM each step kernel is compiled for (its register
+// budget), measured per instantiation with 32 x 4 tiles at 2048^2 (2400 x 600
+// for walls), MLUPS at 8 / 9 / 10 blocks:
+//   FP32 periodic 38.7 / 38.6 / 39.4 k; FP32 walls 32.1 / 31.9 / 31.3 k (spills);
+//   16-bit periodic 46.5 / 47.6 / 43.6 k; 16-bit walls 41.2 / 42.1 / 42.7 k.
+// LBM_STEP_MINB > 0 overrides all of them.
+template <bool FIELDS, int WALLS, int ST>
+constexpr int step_minb() {
+    if (LBM_STEP_MINB > 0) return LBM_STEP_MINB;
+    if (FIELDS) return 8;
+    if (ST == ST_FP32) return WALLS == 0 ? 10 : 8;
+    return WALLS == 0 ? 9 : 10;
+}
+
 template <int TX, int TY, bool FIELDS, int WALLS, int ST>
-__global__ void __launch_bounds__(TX* TY, LBM_STEP_MINB)
+__global__ void __launch_bounds__(TX* TY, (step_minb<FIELDS, WALLS, ST>()))
     k_step(const float* __restrict__ fs, const float* __restrict__ gs, float* __restrict__ fd,
            float* __restrict__ gd, float* __restrict__ phiu, unsigned int* __restrict__ flag,
            double* __restrict__ out, int nx, int ny, Model m, int pf_ahead) {
@@ -197,6 +215,12 @@ __global__ void __launch_bounds__(TX* TY, LBM_STEP_MINB)
             if (lin < gridDim.x * gridDim.y)
                 prefetch_tile<TX, TY, ST>(fs, gs, phiu, nx, ny, WALLS >= 0 ? WALLS : m.walls,
                                           lin % gridDim.x, lin / gridDim.x);
+#if LBM_PREFETCH_TWICE
+            const int lin2 = lin + pf_ahead;
+            if (lin2 < gridDim.x * gridDim.y)
+                prefetch_tile<TX, TY, ST>(fs, gs, phiu, nx, ny, WALLS >= 0 ? WALLS : m.walls,
+                                          lin2 % gridDim.x, lin2 / gridDim.x);
+#endif
         }
     }
     step_tile<TX, TY, FIELDS, WALLS, ST>(sphi, fs, gs, fd, gd, phiu, flag, out, nx, ny, m,

@@ -31,6 +31,10 @@
 // warp-uniform branch the run-time-wall kernels use (1).  With 32 x 8 tiles
 // the selects were 5% faster; with the 32 x 4 tiles the branch is (walled
 // impact 2400 x 600, FP16: 39.1 k -> 40.1-41.0 k MLUPS).
+// FP32 population stores with the evict-first (streaming) cache hint
+#ifndef LBM_STORE_STREAMING
+#define LBM_STORE_STREAMING 0
+#endif
 #ifndef LBM_WALL_BRANCH
 #define LBM_WALL_BRANCH 1
 #endif
@@ -55,6 +59,15 @@ struct Pop<ST_FP32> {
                                 const float g[9], float phi) {
         float* F = static_cast<float*>(fb);
         float* G = static_cast<float*>(gb);
+#if LBM_STORE_STREAMING
+        __stcs(F + idx, sub(phi, sum8(f)));
+        __stcs(G + idx, g[0]);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            __stcs(F + (i * N + idx), f[i]);
+            __stcs(G + (i * N + idx), g[i]);
+        }
+#else
         F[idx] = sub(phi, sum8(f));
         G[idx] = g[0];
 #pragma unroll
@@ -62,6 +75,7 @@ struct Pop<ST_FP32> {
             F[i * N + idx] = f[i];
             G[i * N + idx] = g[i];
         }
+#endif
     }
     // one plane entry (checkpoint and initial-state permutations); the rest
     // population's correction is zero in FP32
