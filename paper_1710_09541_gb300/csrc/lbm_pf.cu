@@ -1084,9 +1084,12 @@ struct BatchTable {
 static_assert(sizeof(BatchTable) <= 32000, "kernel parameters are limited to 32 KB");
 
 // resident threads per SM the batch kernels are compiled for (sets the
-// register budget)
+// register budget): 1280 = 10 blocks of 32 x 4, 48 registers, no spills.  On
+// the 64-case sweep (MLUPS, FP32 / FP16 / BF16): 1024 threads 36.1 / 45.0 /
+// 44.3 k, 1152: 36.8 / 47.6 / 46.6 k, 1280: 37.8 / 49.0 / 47.8 k; from 1408
+// the kernels spill.
 #ifndef LBM_BATCH_THREADS
-#define LBM_BATCH_THREADS 1024
+#define LBM_BATCH_THREADS 1280
 #endif
 
 // One time step of every case of one boundary class (WALLS = 0: periodic in
