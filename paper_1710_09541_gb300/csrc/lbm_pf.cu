@@ -70,10 +70,12 @@ struct Ring {
 #define LBM_EARLY_PHIU 1
 #endif
 // L2 prefetch distance of the step kernel in tiles, per 10 SMs (0: off);
-// 30 = 3 tiles of 32 x 4 per SM, about a third of a resident wave at 8
-// blocks/SM (measured best of 20 / 30 / 40 / 60)
+// 20 = 2 tiles of 32 x 4 per SM, about a fifth of a resident wave at 10
+// blocks/SM.  Measured at 2, 2.5, 3, 3.5 tiles per SM: 38.97 / 39.00 / 38.80 /
+// 38.65 k MLUPS at 2048^2 and 33.1 / 32.6 / 32.0 / 31.8 k on the 2400 x 600
+// walled impact.
 #ifndef LBM_PREFETCH_PER10SM
-#define LBM_PREFETCH_PER10SM 30
+#define LBM_PREFETCH_PER10SM 20
 #endif
 // prefetch with 16-bit storage too (off: those steps are instruction-bound,
 // and the requests cost more than they hide, 44.5 k -> 43.5 k MLUPS for FP16
