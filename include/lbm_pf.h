@@ -280,6 +280,22 @@ const char* lbm_batch_last_error(const lbm_batch* b);
  *   node outside the grid: nothing is written), LBM_ERR_STATE, LBM_ERR_CUDA.
  */
 lbm_status lbm_spreading_radius(lbm_handle* h, int y, int xc, double* r, double* r_interp);
+
+/*
+ * lbm_laplace_jump -- the pressure jump of a drop (the Laplace law, p_in -
+ *   p_out = sigma / R, that Eqs. 5-7 and 22 reproduce for a resolved
+ *   interface): the mean of p (Eq. 22b) over the nodes closer than r_in to
+ *   (xc, yc) minus its mean over the nodes farther than r_out, summed in FP64
+ *   on the device.  Node (i, j) sits at (i, j); distances take the nearest
+ *   periodic image along periodic directions.  Averaging over the inner
+ *   region rather than reading the centre node matters: with the central
+ *   normal (Eq. 2 with Eq. 27) phi dips at the centre of larger drops and the
+ *   pressure spikes there.  Blocks until the result is on the host.
+ *   Errors: LBM_ERR_INVALID (NULL handle or output, r_in <= 0, r_out < r_in,
+ *   non-finite centre, or an empty region), LBM_ERR_STATE, LBM_ERR_CUDA.
+ */
+lbm_status lbm_laplace_jump(lbm_handle* h, double xc, double yc, double r_in, double r_out,
+                            double* dp);
 lbm_status lbm_probe(lbm_handle* h, int npts, const int* x, const int* y, double* phi, double* rho,
                      double* ux, double* uy, double* p);
 

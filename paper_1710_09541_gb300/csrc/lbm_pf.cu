@@ -1634,9 +1634,90 @@ __global__ void k_probe(const void* __restrict__ fs, const void* __restrict__ gs
     }
 }
 
+// Pressure averages inside r < r_in and outside r > r_out of (xc, yc) over
+// the fields buffer (p is plane 4), with the minimum-image distance along
+// periodic directions: block partials (sum in, count in, sum out, count out)
+// into part, then one block folds them in a fixed order into res.
+__global__ void __launch_bounds__(RED_THREADS)
+    k_jump_partial(const double* __restrict__ fields, int nx, int ny, int periodic_y, double xc,
+                   double yc, double r_in2, double r_out2, double* __restrict__ part) {
+    __shared__ double s[4][RED_THREADS];
+    const size_t N = (size_t)nx * ny;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (size_t n = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * RED_THREADS) {
+        double dx = (double)(n % nx) - xc, dy = (double)(n / nx) - yc;
+        dx -= nx * rint(dx / nx);
+        if (periodic_y) dy -= ny * rint(dy / ny);
+        const double r2 = dx * dx + dy * dy, p = fields[4 * N + n];
+        if (r2 < r_in2) {
+            a[0] += p;
+            a[1] += 1.0;
+        } else if (r2 > r_out2) {
+            a[2] += p;
+            a[3] += 1.0;
+        }
+    }
+    const int t = threadIdx.x;
+    for (int k = 0; k < 4; ++k) s[k][t] = a[k];
+    __syncthreads();
+    for (int h = RED_THREADS / 2; h > 0; h >>= 1) {
+        if (t < h)
+            for (int k = 0; k < 4; ++k) s[k][t] += s[k][t + h];
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int k = 0; k < 4; ++k) part[4 * blockIdx.x + k] = s[k][0];
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_jump_final(const double* __restrict__ part, int nb, double* __restrict__ res) {
+    __shared__ double s[4][RED_THREADS];
+    const int t = threadIdx.x;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = t; b < nb; b += RED_THREADS)
+        for (int k = 0; k < 4; ++k) a[k] += part[4 * b + k];
+    for (int k = 0; k < 4; ++k) s[k][t] = a[k];
+    __syncthreads();
+    for (int h = RED_THREADS / 2; h > 0; h >>= 1) {
+        if (t < h)
+            for (int k = 0; k < 4; ++k) s[k][t] += s[k][t + h];
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int k = 0; k < 4; ++k) res[k] = s[k][0];
+}
+
 }  // namespace
 
 extern "C" {
+
+lbm_status lbm_laplace_jump(lbm_handle* h, double xc, double yc, double r_in, double r_out,
+                            double* dp) {
+    if (!h) return LBM_ERR_INVALID;
+    if (!dp) return fail(h, LBM_ERR_INVALID, "lbm_laplace_jump: NULL output");
+    if (!h->inited) return fail(h, LBM_ERR_STATE, "lbm_laplace_jump before lbm_init");
+    if (!(r_in > 0) || !(r_out >= r_in) || !std::isfinite(xc) || !std::isfinite(yc) ||
+        !std::isfinite(r_out))
+        return fail(h, LBM_ERR_INVALID, "lbm_laplace_jump: need finite centre and 0 < r_in <= r_out");
+    LBM_CUDA(h, cudaSetDevice(h->device));
+    double* buf = (double*)h->staging;
+    lbm_status st = launch_step(h, true, buf);
+    if (st != LBM_OK) return st;
+    k_jump_partial<<<RED_BLOCKS, RED_THREADS, 0, h->stream>>>(buf, h->nx, h->ny, h->model.walls == 0,
+                                                               xc, yc, r_in * r_in, r_out * r_out,
+                                                               h->red_part);
+    LBM_CUDA(h, cudaGetLastError());
+    k_jump_final<<<1, RED_THREADS, 0, h->stream>>>(h->red_part, RED_BLOCKS, h->red_res);
+    LBM_CUDA(h, cudaGetLastError());
+    double r[4];
+    LBM_CUDA(h, cudaMemcpyAsync(r, h->red_res, sizeof r, cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (r[1] == 0.0 || r[3] == 0.0)
+        return fail(h, LBM_ERR_INVALID, "lbm_laplace_jump: no node inside r_in or outside r_out");
+    *dp = r[0] / r[1] - r[2] / r[3];
+    return LBM_OK;
+}
 
 lbm_status lbm_spreading_radius(lbm_handle* h, int y, int xc, double* r, double* r_interp) {
     if (!h) return LBM_ERR_INVALID;

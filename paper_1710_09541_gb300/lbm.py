@@ -33,7 +33,8 @@ EXPORTS = ("lbm_create", "lbm_init", "lbm_step", "lbm_get_fields", "lbm_state_by
            "lbm_get_state", "lbm_set_state", "lbm_diag", "lbm_synchronize", "lbm_destroy",
            "lbm_last_error", "lbm_diag_fields_noalloc", "lbm_batch_create", "lbm_batch_step",
            "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error",
-           "lbm_spreading_radius", "lbm_probe", "lbm_workspace_bytes", "lbm_create_in")
+           "lbm_spreading_radius", "lbm_probe", "lbm_workspace_bytes", "lbm_create_in",
+           "lbm_laplace_jump")
 
 
 class LbmError(RuntimeError):
@@ -86,6 +87,8 @@ def load() -> ctypes.CDLL:
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_diag_fields_noalloc.argtypes = [vp, sz, vp, vp, ctypes.c_char_p, sz]
     L.lbm_spreading_radius.argtypes = [vp, i, i, pd, pd]
+    L.lbm_laplace_jump.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, pd]
     L.lbm_workspace_bytes.argtypes = [i, i, ctypes.POINTER(lbm_params), ctypes.POINTER(sz)]
     L.lbm_create_in.argtypes = [i, i, ctypes.POINTER(lbm_params), vp, sz, ctypes.POINTER(vp)]
     pi = ctypes.POINTER(ctypes.c_int)
@@ -242,6 +245,13 @@ class Lattice:
         self._check(self._L.lbm_spreading_radius(self._h, int(y), xc, ctypes.byref(r),
                                                  ctypes.byref(ri)))
         return r.value, ri.value
+
+    def laplace_jump(self, xc: float, yc: float, r_in: float, r_out: float) -> float:
+        """Mean p inside r_in of (xc, yc) minus mean p outside r_out (lbm_laplace_jump)."""
+        dp = ctypes.c_double()
+        self._check(self._L.lbm_laplace_jump(self._h, float(xc), float(yc), float(r_in),
+                                             float(r_out), ctypes.byref(dp)))
+        return dp.value
 
     def probe(self, x, y):
         """Fields at nodes (x[j], y[j]): dict of float64 arrays phi, rho, ux, uy, p."""

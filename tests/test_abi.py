@@ -121,5 +121,6 @@ def test_null_handle_calls_are_rejected(L):
     assert L.lbm_diag(None, None, None, None, None) == lbm.LBM_ERR_INVALID
     assert L.lbm_state_bytes(None) == 0
     assert L.lbm_spreading_radius(None, 0, 0, None, None) == lbm.LBM_ERR_INVALID
+    assert L.lbm_laplace_jump(None, 0.0, 0.0, 1.0, 2.0, None) == lbm.LBM_ERR_INVALID
     assert L.lbm_probe(None, 0, None, None, None, None, None, None, None) == lbm.LBM_ERR_INVALID
     L.lbm_destroy(None)

@@ -82,3 +82,59 @@ def test_spreading_radius_definition_and_oracle(lbm, bc, storage):
         assert g.spreading_radius(ny - 2) == (0.0, 0.0)
         with pytest.raises(lbm.LbmError):
             g.spreading_radius(ny)
+
+
+def _jump_host(p, xc, yc, r_in, r_out, periodic_y):
+    ny, nx = p.shape
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    dx = xx - xc
+    dx -= nx * np.rint(dx / nx)
+    dy = yy - yc
+    if periodic_y:
+        dy -= ny * np.rint(dy / ny)
+    r2 = dx * dx + dy * dy
+    return p[r2 < r_in * r_in].mean() - p[r2 > r_out * r_out].mean()
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_laplace_jump_matches_fields(lbm, bc):
+    """The device reduction equals the same averages taken on the read-back p
+    (FP64 sums in a different order), including a centre near the periodic
+    seam."""
+    nx, ny = 70, 45
+    P = dict(cases.params_static_drop(ratio=100.0), bc_y=bc)
+    # the drop straddles the periodic seam: union of its two images in x
+    phi0 = np.maximum(cases.drop(nx, ny, 11, 4.0, x0=3.0, y0=22.0, walls_y=bc > 0),
+                      cases.drop(nx, ny, 11, 4.0, x0=3.0 + nx, y0=22.0, walls_y=bc > 0))
+    with lbm.Lattice(nx, ny, **P) as g:
+        g.init(phi0).step(300)
+        assert np.isfinite(g.diag()[0])
+        p = g.fields()["p"]
+        for xc, yc, ri, ro in ((3.0, 22.0, 5.5, 20.0), (35.0, 22.0, 3.0, 25.0)):
+            got = g.laplace_jump(xc, yc, ri, ro)
+            ref = _jump_host(p, xc, yc, ri, ro, bc == 0)
+            assert abs(got - ref) <= 1e-12 * max(abs(ref), 1e-12), (got, ref)
+        for bad in ((3.0, 22.0, 0.0, 5.0), (3.0, 22.0, 6.0, 5.0), (3.3, 22.3, 0.2, 5.0)):
+            with pytest.raises(lbm.LbmError) as e:
+                g.laplace_jump(*bad)
+            assert e.value.status == lbm.LBM_ERR_INVALID
+
+
+def test_laplace_jump_resolved_drop_vs_oracle(lbm):
+    """A resolved drop (W = 8, R = 20, 96 x 96, ratio 1000, sigma = 0.01):
+    the time-averaged device jump follows the FP64 oracle's within 1% and the
+    Laplace law sigma/R within 3%."""
+    n, R = 96, 20
+    P = dict(cases.params_static_drop(), W=8.0)
+    phi0 = cases.drop(n, n, R, 8.0)
+    o = oracle.Lattice(n, n, **P).init(phi0).step(8000)
+    got, ref = [], []
+    with lbm.Lattice(n, n, **P) as g:
+        g.init(phi0).step(8000)
+        for _ in range(16):
+            g.step(125)
+            o.step(125)
+            got.append(g.laplace_jump(n / 2, n / 2, R / 2, R + 12))
+            ref.append(_jump_host(o.fields()["p"], n / 2, n / 2, R / 2, R + 12, True))
+    assert abs(np.mean(got) / np.mean(ref) - 1) < 0.01
+    assert abs(np.mean(got) * R / 0.01 - 1) < 0.03
