@@ -78,8 +78,8 @@ struct Ring {
 #define LBM_PREFETCH_PER10SM 20
 #endif
 // prefetch with 16-bit storage too (off: those steps are instruction-bound,
-// and the requests cost more than they hide, 44.5 k -> 43.5 k MLUPS for FP16
-// at 2048^2 with the paired layout)
+// and the requests cost more than they hide: FP16 at 2048^2 47.6 k -> 45.5 k
+// MLUPS, BF16 47.5 k -> 44.5 k, at their tuned residency)
 #ifndef LBM_PREFETCH_16
 #define LBM_PREFETCH_16 0
 #endif
