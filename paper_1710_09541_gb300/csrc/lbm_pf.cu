@@ -64,6 +64,24 @@ struct Ring {
 #ifndef LBM_STEP_MINB
 #define LBM_STEP_MINB 0
 #endif
+// Debug build (LBM_DEBUG_CHECKS = 1, the library liblbm_pf_debug.so): the
+// step checks every neighbour row and column and every shared-memory slot it
+// computes, records an out-of-range one as bit 4 of the error flag (the call
+// returns LBM_ERR_CUDA) and skips it, and poisons the tile's phi slots with
+// NaN before filling them.  It stands in for a sanitizer: the arithmetic is
+// the same, so results equal the release library's bit for bit.
+#ifndef LBM_DEBUG_CHECKS
+#define LBM_DEBUG_CHECKS 0
+#endif
+#if LBM_DEBUG_CHECKS
+__device__ __forceinline__ bool nbr_in_range(const Nbr& q, int nx, int ny) {
+    const int last = (ny - 1) * nx;
+    auto row = [&](int r) { return r >= 0 && r <= last && r % nx == 0; };
+    auto col = [&](int c) { return c >= 0 && c < nx; };
+    return row(q.r0) && row(q.rm) && row(q.rp) && col(q.x) && col(q.xm) && col(q.xp);
+}
+#endif
+
 // load (phi u) of the previous step with the node's pulls instead of just
 // before the collision
 #ifndef LBM_EARLY_PHIU
@@ -115,8 +133,21 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
 #if LBM_EARLY_PHIU
     float2 prev = make_float2(0.f, 0.f);
 #endif
+#if LBM_DEBUG_CHECKS
+    // poison the tile's phi slots: a slot that phase 1 fails to write reaches
+    // the stencil as NaN and trips the non-finite check
+    for (int k = ty * TX + tx; k < (TY + 2) * (TX + 2); k += TX * TY)
+        (&sphi[0][0])[k] = __int_as_float(0x7fc00000);
+    __syncthreads();
+#endif
     if (active) {
         q = make_nbr<WALLS>(x, y, nx, ny, m.walls);
+#if LBM_DEBUG_CHECKS
+        if (!nbr_in_range(q, nx, ny)) {  // record, and pull node 0 instead
+            atomicOr(flag, 4u);
+            q = make_nbr<WALLS>(0, 0, nx, ny, m.walls);
+        }
+#endif
 #if LBM_EARLY_PHIU
         if (!FIELDS) prev = make_float2(phiu[q.r0 + x], phiu[N32 + q.r0 + x]);
 #endif
@@ -129,6 +160,13 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
     for (int r = ty * TX + tx; r < Ring<TX, TY>::count; r += TX * TY) {
         int lx, ly;
         Ring<TX, TY>::pos(r, lx, ly);
+#if LBM_DEBUG_CHECKS
+        const int fx = fold_x(x0 + lx, nx), fy = fold_y(y0 + ly, ny, wfold);
+        if (lx < -1 || lx > TX || ly < -1 || ly > TY || fx < 0 || fx >= nx || fy < 0 || fy >= ny) {
+            atomicOr(flag, 4u);
+            continue;
+        }
+#endif
         sphi[ly + 1][lx + 1] = phi_at_st<ST, WALLS>(fs, N32, fold_x(x0 + lx, nx),
                                                     fold_y(y0 + ly, ny, wfold), nx, ny, m.walls);
     }
@@ -650,6 +688,8 @@ static lbm_status check_flag(lbm_handle* h) {
         LBM_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(unsigned int), h->stream));
         if (v & 2u)
             return fail(h, LBM_ERR_CUDA, "a bulk tensor copy did not complete within the wait limit");
+        if (v & 4u)
+            return fail(h, LBM_ERR_CUDA, "an index check of the debug build failed");
         return fail(h, LBM_ERR_NONFINITE, "non-finite phi, u or p produced by a step");
     }
     return LBM_OK;
@@ -1102,6 +1142,14 @@ __global__ void __launch_bounds__(TX* TY, LBM_BATCH_THREADS / (TX * TY))
     k_step_batch(const __grid_constant__ BatchTable T, const int2* __restrict__ tiles, int parity) {
     __shared__ float sphi[TY + 2][TX + 2];
     const int2 e = __ldg(tiles + blockIdx.x);
+#if LBM_DEBUG_CHECKS
+    if (e.x < 0 || e.x >= T.ncases || (e.y & 0xffff) * TX >= T.c[e.x < 0 || e.x >= T.ncases ? 0 : e.x].nx ||
+        (e.y >> 16) * TY >= T.c[e.x < 0 || e.x >= T.ncases ? 0 : e.x].ny) {
+        if (e.x >= 0 && e.x < T.ncases) atomicOr(T.c[e.x].flag, 4u);
+        else atomicOr(T.c[0].flag, 4u);
+        return;  // the whole block leaves before its barrier
+    }
+#endif
     const CaseDesc& cd = T.c[e.x];
     const int x0 = (e.y & 0xffff) * TX, y0 = (e.y >> 16) * TY;
     const int c = (cd.cur + parity) & 1;
@@ -1533,6 +1581,12 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
         LBM_BCUDA(b, cudaMemcpyAsync(fl.data(), b->d_flags, b->ncases * sizeof(unsigned int),
                                      cudaMemcpyDeviceToHost, b->bs[0]));
         LBM_BCUDA(b, cudaStreamSynchronize(b->bs[0]));
+        for (int c = 0; c < b->ncases; ++c)
+            if (fl[c] & 4u) {
+                LBM_BCUDA(b, cudaEventRecord(b->ev_out, b->bs[0]));
+                LBM_BCUDA(b, cudaStreamWaitEvent(b->user, b->ev_out, 0));
+                return bfail(b, LBM_ERR_CUDA, "case %d: an index check of the debug build failed", c);
+            }
         for (int c = 0; c < b->ncases; ++c)
             if (fl[c] && b->cases[c]->prm.check_every > 0) {
                 LBM_BCUDA(b, cudaEventRecord(b->ev_out, b->bs[0]));
