@@ -299,6 +299,19 @@ lbm_status lbm_laplace_jump(lbm_handle* h, double xc, double yc, double r_in, do
 lbm_status lbm_probe(lbm_handle* h, int npts, const int* x, const int* y, double* phi, double* rho,
                      double* ux, double* uy, double* p);
 
+/*
+ * lbm_selftest_bounded_wait -- exercise the timeout path of the bounded
+ *   mbarrier waits of the TMA-staged step kernel: a one-block kernel arms an
+ *   mbarrier for bytes that no copy will deliver (none is issued), waits with
+ *   the kernel's own bounded-wait routine and a short limit, and records the
+ *   timeout the way the staged kernel does.  *timed_out = 1 when the wait gave
+ *   up (the expected result), after which the device stays usable.  The paper
+ *   has no counterpart; this checks this library's failure handling.
+ *   stream: cudaStream_t or NULL.  Errors: LBM_ERR_INVALID (NULL output),
+ *   LBM_ERR_CUDA.
+ */
+lbm_status lbm_selftest_bounded_wait(void* stream, int* timed_out);
+
 /* lbm_synchronize -- wait for all work enqueued by this handle. */
 lbm_status lbm_synchronize(lbm_handle* h);
 

@@ -1746,6 +1746,29 @@ __global__ void __launch_bounds__(RED_THREADS)
 
 extern "C" {
 
+lbm_status lbm_selftest_bounded_wait(void* stream, int* timed_out) {
+    if (!timed_out) return LBM_ERR_INVALID;
+    *timed_out = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int* d = nullptr;
+    unsigned int v = 0;
+    cudaError_t e = cudaMalloc(&d, sizeof v);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof v, s);
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32, 0, s>>>(d, 4096);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, d, sizeof v, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "lbm_selftest_bounded_wait: %s\n", cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    *timed_out = (v & 2u) ? 1 : 0;
+    return LBM_OK;
+}
+
 lbm_status lbm_laplace_jump(lbm_handle* h, double xc, double yc, double r_in, double r_out,
                             double* dp) {
     if (!h) return LBM_ERR_INVALID;

@@ -49,10 +49,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (long long it = 0; it < TMA_WAIT_LIMIT; ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long limit = TMA_WAIT_LIMIT) {
+    for (long long it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// Self-test of the bounded wait: an mbarrier armed for 16 transaction bytes
+// that no copy will deliver (none is issued, so nothing is in flight), then
+// the same bounded wait the staged kernel uses, with a short limit.  A wait
+// that gives up sets bit 1 of *flag (as in the staged kernel) and the block
+// returns.
+__global__ void k_wait_selftest(unsigned int* flag, long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    mbar_arrive_expect_tx(&bar, 16);
+    if (!mbar_wait_bounded(&bar, 0, limit)) atomicOr(flag, 2u);
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y, int z) {
