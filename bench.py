@@ -174,6 +174,9 @@ def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return
+    import oracle
+
+    cores = oracle.set_threads(_cores())
     nx = cases.PERF_NX
     phi_full, params = cases.perf_case()
     total = args.steps + args.warmup
@@ -198,7 +201,7 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": "perf-2048: spinodal-like 2048x2048 periodic D2Q9, density ratio 1000",
                    "nx": nx, "ny": cases.PERF_NY, "sample_rows": rows},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -395,9 +398,18 @@ def run_ours(args):
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             rows = 256
+            import oracle
+
+            cores = oracle.set_threads(_cores())
             rate, n, dt = _oracle_rate(nx, rows, params, phi0[:rows], args.cpu_seconds)
-            cpu = {"value": rate, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"periodic {nx}x{rows} strip of the workload, {n} steps in {dt:.1f} s"}
+            # the same oracle on one thread, on a narrower strip for ~3 s
+            oracle.set_threads(1)
+            r1, n1, dt1 = _oracle_rate(nx, 32, params, phi0[:32], 3.0)
+            oracle.set_threads(cores)
+            cpu["single_thread"] = {"value": r1, "unit": UNIT, "cores": 1,
+                                    "sample": f"periodic {nx}x32 strip, {n1} steps in {dt1:.1f} s"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,

@@ -82,6 +82,8 @@ def lib() -> ctypes.CDLL:
             L.orc_destroy.argtypes = [vp]
             L.orc_init.argtypes = [vp, pd, pd, pd, pd]
             L.orc_step.argtypes = [vp, ctypes.c_int]
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_set_threads.restype = ctypes.c_int
             L.orc_get_fields.argtypes = [vp, pd, pd, pd, pd, pd, pd]
             L.orc_get_state.argtypes = [vp, pd]
             L.orc_set_state.argtypes = [vp, pd]
@@ -137,6 +139,11 @@ def force_g(tau_g, drho, ux, uy, gpx, gpy, Fx, Fy):
     out = np.zeros(9)
     lib().orc_force_g(tau_g, drho, ux, uy, gpx, gpy, Fx, Fy, _ptr(out))
     return out
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops; returns the count now in use."""
+    return lib().orc_set_threads(int(n))
 
 
 def grad_lap(phi, bc_y=0):

@@ -49,6 +49,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---- D2Q9 lattice, Eq. 10 (velocity order of the paper) ----------------- */
 static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -428,6 +431,19 @@ static void one_step(orc_lattice* L) {
     double* t;
     t = L->f; L->f = L->fs; L->fs = t;
     t = L->g; L->g = L->gs; L->gs = t;
+}
+
+/* Threads of the OpenMP loops (n >= 1); returns the count in use, 1 without
+ * OpenMP.  The results do not depend on it (every node is independent and
+ * the only global sum is serial). */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 int orc_step(orc_lattice* L, int nsteps) {
