@@ -128,7 +128,13 @@ class ClockSampler:
         if self.proc is None:
             return None
         rows = []
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) != 7:
                 continue
