@@ -128,8 +128,11 @@ class ClockSampler:
         if self.proc is None:
             return None
         rows = []
-        with open(self.path) as fh:
-            lines = fh.readlines()
+        try:
+            with open(self.path) as fh:
+                lines = fh.readlines()
+        except OSError:
+            return None
         try:
             os.remove(self.path)
         except OSError:
