@@ -148,6 +148,42 @@ def test_laplace_law_resolved_interface(normal_scheme):
     assert abs(slope / 0.01 - 1) < 0.03
 
 
+def interface_height(col):
+    """Height of the phi = 1/2 crossing in a column with liquid below, by
+    linear interpolation between node centres y_j = j + 1/2."""
+    j = int(np.nonzero((col[:-1] >= 0.5) & (col[1:] < 0.5))[0][0])
+    return j + 0.5 + (col[j] - 0.5) / (col[j] - col[j + 1])
+
+
+@pytest.mark.parametrize("ny,ratio", [(64, 1000.0), (63, 1000.0), (64, 10.0)])
+def test_planar_interface_at_rest_stays_put(ny, ratio):
+    """A flat layer between walls (the Eq. 33 geometry without the body
+    force) has zero curvature, so nothing drives it.  Over 1e4 steps:
+    - the phi = 1/2 crossing moves by less than 1e-4 node (measured at most
+      1.5e-5; the interface sits on a node for odd ny, between nodes for even);
+    - the pressure jump across it stays below 1e-7, the Laplace law at
+      R -> inf (sigma / W = 2.5e-4; measured 4e-8);
+    - phi stays within 1e-2 of Eq. 33's tanh (the W = 4 lattice profile of
+      Eqs. 3, 6 and 7 differs from it by 6e-3);
+    - the spurious speed stays below 5e-6 (measured 1.5e-6 at ratio 10, the
+      slowest to settle).
+    Catches a wrong lambda (Eq. 3) or sharpening direction (the profile
+    widens or moves), a wrong k, beta or sign in Eqs. 6-7 (a chemical-
+    potential force on the flat layer: a jump of 2e-7 to 1e-6 and flow), and
+    a wrong sign of the interface term of Eq. 22b (flow)."""
+    P = cases.params_poiseuille(ny, ratio=ratio, Gx=0.0, W=4.0)
+    phi0 = cases.layer(4, ny, 4.0)
+    lat = _lattice(4, ny, **P).init(phi0)
+    h0 = interface_height(lat.fields()["phi"][:, 0])
+    lat.step(10000)
+    F = lat.fields()
+    assert abs(interface_height(F["phi"][:, 0]) - h0) < 1e-4
+    p = F["p"][:, 0]
+    assert abs(p[4:12].mean() - p[-12:-4].mean()) < 1e-7
+    assert np.abs(F["phi"] - phi0).max() < 1e-2
+    assert np.hypot(F["ux"], F["uy"]).max() < 5e-6
+
+
 def _poiseuille(ny, nx, params, steps, u_start):
     lat = _lattice(nx, ny, **params).init(cases.layer(nx, ny, params["W"]),
                                           np.broadcast_to(u_start[:, None], (ny, nx)))
