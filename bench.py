@@ -332,6 +332,20 @@ def run_storage_variants(torch, lbm, stream, steps):
     return out
 
 
+def run_data_variants(torch, lbm, stream, steps):
+    """The 2048 x 2048 grid with other data on the same FP32 path: one static
+    drop of R = 512 (mostly bulk) against the spinodal-like headline
+    (interfaces everywhere)."""
+    nx, ny = cases.PERF_NX, cases.PERF_NY
+    phi0, params = cases.perf_drop_case()
+    lat = lbm.Lattice(nx, ny, stream=stream, **params).init(phi0)
+    lat.step(50)
+    t = _time_steps(torch, stream, lambda: lat.step(steps))
+    lat.close()
+    return {"perf-2048-drop": {"value": nx * ny * steps / t / 1e6, "unit": UNIT, "steps": steps,
+                               "workload": "static drop R = 512, W = 4, ratio 1000, FP32 storage"}}
+
+
 def run_ours(args):
     import torch
 
@@ -392,10 +406,11 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     lat.close()
 
-    batched = storage_variants = None
+    batched = storage_variants = data_variants = None
     if not args.no_batched:
         batched = run_batched(torch, lbm, stream, args.batch_steps)
         storage_variants = run_storage_variants(torch, lbm, stream, 2000)
+        data_variants = run_data_variants(torch, lbm, stream, 2000)
 
     t_dev, t_e2e = max_over_ranks([ms / 1e3, e2e_s], dist, "cuda")
 
@@ -442,6 +457,7 @@ def run_ours(args):
             "sum_phi": s_phi, "umax": umax,
             "batched": batched,
             "single_case_storage": storage_variants,
+            "data_variants": data_variants,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -135,6 +135,14 @@ def perf_case(nx=PERF_NX, ny=PERF_NY, seed=1):
     return spinodal(nx, ny, 0.5, 0.01, seed), params
 
 
+def perf_drop_case(nx=PERF_NX, ny=PERF_NY, R=512.0):
+    """The 2048 x 2048 grid holding one static drop of radius R (W = 4, the
+    static-drop parameters): mostly bulk, against the perf case's interfaces
+    everywhere, so that the two together show whether the step's speed
+    depends on the data."""
+    return drop(nx, ny, R, 4.0), params_static_drop()
+
+
 def batch_cases(n=64, seed=7):
     """The batched sweep: n independent cases, half static drops (periodic) and
     half droplet impacts (walls), on uneven grids from 256 x 256 to
@@ -173,5 +181,5 @@ __all__ = [
     "splitmix64", "uniform01", "drop", "layer", "spinodal", "impact",
     "params_static_drop", "params_poiseuille",
     "params_spinodal", "params_impact", "perf_case", "batch_cases", "capillary_velocity",
-    "PERF_NX", "PERF_NY",
+    "PERF_NX", "PERF_NY", "perf_drop_case",
 ]

@@ -25,7 +25,7 @@ def test_bench_line_has_the_contract_keys():
     d = json.loads(lines[0])
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
               "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "clocks",
-              "gpu_launches", "batched", "single_case_storage"):
+              "gpu_launches", "batched", "single_case_storage", "data_variants"):
         assert k in d, k
     assert d["unit"] == "MLUPS" and d["steps"] == 40 and d["warmup"] == 3 and d["gpu_launches"] == 40
     N = d["config"]["nx"] * d["config"]["ny"]
@@ -40,3 +40,4 @@ def test_bench_line_has_the_contract_keys():
     assert b["cases"] == 64 and b["value"] > 0 and b["sequential_fp32"] > 0 and b["batched_fp32"] > 0
     assert set(b["tile"]) == {"periodic", "walls"}
     assert d["clocks"] is None or "sm_mhz" in d["clocks"]
+    assert d["data_variants"]["perf-2048-drop"]["value"] > 0
