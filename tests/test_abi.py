@@ -68,7 +68,10 @@ def test_create_rejects_bad_parameters(L, bad):
     assert not h.value
 
 
-@pytest.mark.parametrize("nx,ny", [(0, 4), (4, 0), (-3, 5), (1 << 20, 1 << 20)])
+# nx * ny must stay below floor(2^31 / 20) = 107374182 so that every 32-bit
+# index of the 20-plane state permutation fits; one node past the limit fails
+@pytest.mark.parametrize("nx,ny", [(0, 4), (4, 0), (-3, 5), (1 << 20, 1 << 20), (1, 107374182),
+                                   (107374182, 1), (16384, 6554)])
 def test_create_rejects_bad_sizes(L, nx, ny):
     p = lbm.make_params()
     h = ctypes.c_void_p()
