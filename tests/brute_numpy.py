@@ -86,12 +86,21 @@ def step(f, g, phiu, p):
     tau_g = 3 * nu_of(phi, p) + 0.5
     drho = p["rho_l"] - p["rho_g"]
     lam = 4 * phi * (1 - phi) / p["W"]
-    mag = np.hypot(m["gx"], m["gy"])
-    safe = np.where(mag > 1e-6, mag, 1.0)
-    nxv = np.where(mag > 1e-6, m["gx"] / safe, 0.0)
-    nyv = np.where(mag > 1e-6, m["gy"] / safe, 0.0)
     Dx = phi * ux - phiu[0]
     Dy = phi * uy - phiu[1]
+    if p.get("normal_scheme", 0) == 1:
+        # Eq. 29: n along -C, C = first moment of the non-equilibrium part plus
+        # half the time derivative of phi u
+        neq = [f[i] - W[i] * phi * (1 + 3 * (CX[i] * ux + CY[i] * uy)) for i in range(9)]
+        vx = sum(CX[i] * neq[i] for i in range(9)) + 0.5 * Dx
+        vy = sum(CY[i] * neq[i] for i in range(9)) + 0.5 * Dy
+        vx, vy = -vx, -vy
+    else:
+        vx, vy = m["gx"], m["gy"]
+    mag = np.hypot(vx, vy)
+    safe = np.where(mag > 1e-6, mag, 1.0)
+    nxv = np.where(mag > 1e-6, vx / safe, 0.0)
+    nyv = np.where(mag > 1e-6, vy / safe, 0.0)
     fo = np.empty_like(f)
     go = np.empty_like(g)
     usq = ux ** 2 + uy ** 2

@@ -265,18 +265,19 @@ def test_layered_poiseuille_table1_ratio10():
     assert u[:ny // 2].max() < u[ny // 2:].max()   # the gas layer (upper) moves faster
 
 
-@pytest.mark.parametrize("bc_y", [0, 1, 2])
-def test_brute_force_numpy_transcription(bc_y):
+@pytest.mark.parametrize("bc_y,normal_scheme", [(0, 0), (1, 0), (2, 0), (0, 1), (1, 1)])
+def test_brute_force_numpy_transcription(bc_y, normal_scheme):
     """8 x 8 grids, 10 steps, against the independent whole-array NumPy
-    transcription (catches index and sign slips in either)."""
+    transcription, with the central (Eq. 2 with Eq. 27) or the local (Eq. 29)
+    normal (catches index and sign slips in either)."""
     nx = ny = 8
-    r = np.random.default_rng(7 + bc_y)
+    r = np.random.default_rng(7 + bc_y + 3 * normal_scheme)
     phi0 = cases.drop(nx, ny, 2.5, 3.0, x0=3.7, y0=4.2, walls_y=bool(bc_y)) + 0.01 * r.random((ny, nx))
     ux0 = 0.01 * r.standard_normal((ny, nx))
     uy0 = 0.01 * r.standard_normal((ny, nx))
     p0 = 1e-4 * r.standard_normal((ny, nx))
     P = dict(rho_l=1.0, rho_g=0.01, nu_l=0.05, nu_g=0.2, visc_mode={0: 0, 1: 2, 2: 1}[bc_y],
-             sigma=0.02, W=3.0, tau_h=0.9, Gx=1e-5, Gy=-2e-5, bc_y=bc_y)
+             sigma=0.02, W=3.0, tau_h=0.9, Gx=1e-5, Gy=-2e-5, bc_y=bc_y, normal_scheme=normal_scheme)
     lat = _lattice(nx, ny, **P).init(phi0, ux0, uy0, p0)
     f, g, phiu = bn.init(phi0, ux0, uy0, p0, P)
     of, og, ophiu = lat.get_state()
