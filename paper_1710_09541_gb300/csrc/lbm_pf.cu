@@ -232,14 +232,16 @@ __device__ __forceinline__ void prefetch_tile(const void* fs, const void* gs, co
 // Resident blocks per SM each step kernel is compiled for (its register
 // budget), measured per instantiation with 32 x 4 tiles at 2048^2 (2400 x 600
 // for walls), MLUPS at 8 / 9 / 10 blocks:
-//   FP32 periodic 38.7 / 38.6 / 39.4 k; FP32 walls 32.1 / 31.9 / 31.3 k (spills);
-//   16-bit periodic 46.5 / 47.6 / 43.6 k; 16-bit walls 41.2 / 42.1 / 42.7 k.
+//   FP32 periodic 38.7 / 38.6 / 39.4 k; 16-bit periodic 46.5 / 47.6 / 43.6 k;
+//   16-bit walls 41.2 / 42.1 / 42.7 k (before the source-folded collision);
+//   FP32 walls 32.5 / 33.0 k at 8 / 9 (10 spills), 16-bit periodic 49.4 k at 9
+//   against 44.9 k at 10 (with it).
 // LBM_STEP_MINB > 0 overrides all of them.
 template <bool FIELDS, int WALLS, int ST>
 constexpr int step_minb() {
     if (LBM_STEP_MINB > 0) return LBM_STEP_MINB;
     if (FIELDS) return 8;
-    if (ST == ST_FP32) return WALLS == 0 ? 10 : 8;
+    if (ST == ST_FP32) return WALLS == 0 ? 10 : 9;
     return WALLS == 0 ? 9 : 10;
 }
 
@@ -570,7 +572,7 @@ static Model make_model(const lbm_params& p) {
     m.Gx = (float)p.Gx;
     m.Gy = (float)p.Gy;
     m.inv_tau_f = (float)(1.0 / p.tau_h);
-    m.src_f = (float)(1.0 - 0.5 / p.tau_h);
+    m.tau_f_mh = (float)(p.tau_h - 0.5);
     m.four_over_W = (float)(4.0 / p.W);
     m.nu_l = (float)p.nu_l;
     m.nu_g = (float)p.nu_g;
