@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -127,3 +128,21 @@ def test_null_handle_calls_are_rejected(L):
     assert L.lbm_laplace_jump(None, 0.0, 0.0, 1.0, 2.0, None) == lbm.LBM_ERR_INVALID
     assert L.lbm_probe(None, 0, None, None, None, None, None, None, None) == lbm.LBM_ERR_INVALID
     L.lbm_destroy(None)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the CUDA library the binding raises ImportError; there is no
+    CPU fallback, and nothing in the package imports the oracle."""
+    code = (
+        "import sys\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "from paper_1710_09541_gb300 import cases, lbm\n"
+        f"lbm._LIB_PATH, lbm._lib = {str(tmp_path / 'absent.so')!r}, None\n"
+        "try:\n"
+        "    lbm.Lattice(8, 8)\n"
+        "except ImportError:\n"
+        "    pass\n"
+        "else:\n"
+        "    sys.exit(1)\n"
+        "sys.exit(2 if 'oracle' in sys.modules else 0)\n")
+    assert subprocess.run([sys.executable, "-c", code], cwd=str(tmp_path)).returncode == 0
