@@ -177,6 +177,25 @@ def _cores():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
+def _cpu_model():
+    """The host CPU as /proc/cpuinfo names it ("model name" on x86; the
+    implementer and part codes on Arm), with the machine type."""
+    import platform
+
+    model = None
+    try:
+        info = {}
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            info.setdefault(k.strip(), v.strip())
+        model = info.get("model name") or (
+            f"implementer {info['CPU implementer']} part {info['CPU part']}"
+            if "CPU implementer" in info and "CPU part" in info else None)
+    except OSError:
+        pass
+    return f"{platform.machine()}: {model}" if model else platform.machine()
+
+
 def run_reference(args):
     """The oracle (plain FP64 C, OpenMP over rows) on the host cores, timed on
     a periodic strip of the same workload sized so the whole run stays within
@@ -190,12 +209,12 @@ def run_reference(args):
     nx = cases.PERF_NX
     phi_full, params = cases.perf_case()
     total = args.steps + args.warmup
-    # size the strip from one probe step so (W + K) steps take about 90 s
+    # size the strip from one probe step so (W + K) steps take about
+    # --reference-seconds (90 s by default)
     probe_rows = 64
     rate, _, _ = _oracle_rate(nx, probe_rows, params, phi_full[:probe_rows], 1.0, max_steps=20)
-    rows = int(90.0 * rate * 1e6 / max(total, 1) / nx)
+    rows = int(args.reference_seconds * rate * 1e6 / max(total, 1) / nx)
     rows = int(min(max(rows, 4), cases.PERF_NY))
-    import oracle
 
     lat = oracle.Lattice(nx, rows, **params).init(phi_full[:rows])
     lat.step(args.warmup)
@@ -212,7 +231,7 @@ def run_reference(args):
         "config": {"workload": "perf-2048: spinodal-like 2048x2048 periodic D2Q9, density ratio 1000",
                    "nx": nx, "ny": cases.PERF_NY, "sample_rows": rows},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu": _cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -427,7 +446,7 @@ def run_ours(args):
 
             cores = oracle.set_threads(_cores())
             rate, n, dt = _oracle_rate(nx, rows, params, phi0[:rows], args.cpu_seconds)
-            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": _cpu_model(),
                    "sample": f"periodic {nx}x{rows} strip of the workload, {n} steps in {dt:.1f} s"}
             # the same oracle on one thread, on a narrower strip for ~3 s
             oracle.set_threads(1)
@@ -474,6 +493,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--reference-seconds", type=float, default=90.0,
+                    help="--impl reference: host seconds the warm-up and timed steps should take")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("bench.py: --warmup must be >= 3")
