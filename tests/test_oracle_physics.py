@@ -265,6 +265,33 @@ def test_layered_poiseuille_table1_ratio10():
     assert u[:ny // 2].max() < u[ny // 2:].max()   # the gas layer (upper) moves faster
 
 
+def _layered_Eu(ratio, nu_ratio, ny, W, steps):
+    """E_u (Eq. 32) of the layered Poiseuille flow of Sec. III B on a 4 x ny
+    channel, started from Eq. 31 itself."""
+    rho_l, nu_l, uc, h = 1.0, 0.1, 1e-4, ny / 2
+    P = dict(rho_l=rho_l, rho_g=rho_l / ratio, nu_l=nu_l, nu_g=nu_ratio * nu_l, visc_mode=2, sigma=1e-3,
+             W=W, tau_h=0.8, bc_y=1)
+    P["Gx"] = uc * (rho_l * nu_l + P["rho_g"] * P["nu_g"]) / h ** 2
+    ua = _two_layer_profile(ny, P)
+    u = _poiseuille(ny, 4, P, steps, ua)
+    return np.abs(u - ua).sum() / np.abs(ua).sum()
+
+
+@pytest.mark.parametrize("ratio,nu_ratio", [(100.0, 1.0), (1000.0, 10.0)])
+def test_layered_poiseuille_converges_at_second_order(ratio, nu_ratio):
+    """Table 1's setup (ny = 100, W = 5, step viscosity of Eq. 26) and the
+    same flow on a grid twice as fine (ny = 200, W = 10, four times the
+    steps): E_u against Eq. 31 falls by a factor 4 (measured 4.06 and 3.95;
+    also 3.95 at ratio 10).  The scheme converges to the two-layer solution
+    at second order, so the gap to the paper's E_u is a discretisation
+    constant, not a wrong term (a dropped Lambda term of Eq. 20 leaves E_u
+    near 2 on both grids)."""
+    coarse = _layered_Eu(ratio, nu_ratio, 100, 5.0, 60000)
+    fine = _layered_Eu(ratio, nu_ratio, 200, 10.0, 240000)
+    assert 3.5 < coarse / fine < 4.5, (coarse, fine)
+    assert fine < 3e-2
+
+
 @pytest.mark.parametrize("bc_y,normal_scheme", [(0, 0), (1, 0), (2, 0), (0, 1), (1, 1)])
 def test_brute_force_numpy_transcription(bc_y, normal_scheme):
     """8 x 8 grids, 10 steps, against the independent whole-array NumPy
