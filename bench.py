@@ -185,14 +185,15 @@ def _cpu_model():
     model = None
     try:
         info = {}
-        for line in open("/proc/cpuinfo"):
-            k, _, v = line.partition(":")
-            info.setdefault(k.strip(), v.strip())
+        with open("/proc/cpuinfo", errors="replace") as fh:
+            for line in fh:
+                k, _, v = line.partition(":")
+                info.setdefault(k.strip(), v.strip())
         model = info.get("model name") or (
             f"implementer {info['CPU implementer']} part {info['CPU part']}"
             if "CPU implementer" in info and "CPU part" in info else None)
-    except OSError:
-        pass
+    except Exception:  # the figure is informative only; never fail the run for it
+        model = None
     return f"{platform.machine()}: {model}" if model else platform.machine()
 
 
