@@ -353,17 +353,53 @@ def run_storage_variants(torch, lbm, stream, steps):
 
 
 def run_data_variants(torch, lbm, stream, steps):
-    """The 2048 x 2048 grid with other data on the same FP32 path: one static
-    drop of R = 512 (mostly bulk) against the spinodal-like headline
-    (interfaces everywhere)."""
+    """The same FP32 step on other data and options:
+    - perf-2048-drop: one static drop of R = 512 (mostly bulk) against the
+      spinodal-like headline (interfaces everywhere);
+    - perf-2048-eq29: the headline workload with the local normal of Eq. 29;
+    - impact-2400x600-open-top: the droplet impact (D = 200, Re = 100) with a
+      wall below and the open top (zero-gradient outflow)."""
+    out = {}
     nx, ny = cases.PERF_NX, cases.PERF_NY
-    phi0, params = cases.perf_drop_case()
-    lat = lbm.Lattice(nx, ny, stream=stream, **params).init(phi0)
-    lat.step(50)
-    t = _time_steps(torch, stream, lambda: lat.step(steps))
-    lat.close()
-    return {"perf-2048-drop": {"value": nx * ny * steps / t / 1e6, "unit": UNIT, "steps": steps,
-                               "workload": "static drop R = 512, W = 4, ratio 1000, FP32 storage"}}
+    phi_drop, p_drop = cases.perf_drop_case()
+    phi_perf, p_perf = cases.perf_case()
+    p_imp = dict(cases.params_impact(Re=100.0), bc_y=2)
+    phi_imp, ux_imp, uy_imp = cases.impact(2400, 600, 200.0, 20.0, 0.04, p_imp["W"])
+    runs = [("perf-2048-drop", nx, ny, p_drop, (phi_drop,), "static drop R = 512, W = 4, ratio 1000"),
+            ("perf-2048-eq29", nx, ny, dict(p_perf, normal_scheme=1), (phi_perf,),
+             "perf-2048 with the Eq. 29 normal"),
+            ("impact-2400x600-open-top", 2400, 600, p_imp, (phi_imp, ux_imp, uy_imp),
+             "droplet impact D = 200, Re = 100, ratio 1000, wall below, open top")]
+    for name, gx, gy, params, init, what in runs:
+        lat = lbm.Lattice(gx, gy, stream=stream, **params).init(*init)
+        lat.step(50)
+        t = _time_steps(torch, stream, lambda: lat.step(steps))
+        out[name] = {"value": gx * gy * steps / t / 1e6, "unit": UNIT, "steps": steps,
+                     "workload": what + ", FP32 storage"}
+        if name.startswith("impact"):
+            out["impact_tooling_us"] = _tooling_us(lat, gx, gy)
+        lat.close()
+    return out
+
+
+def _tooling_us(lat, nx, ny, reps=20):
+    """Host wall time per call (microseconds, the call returns its result to
+    the host) of the impact tooling on an nx x ny lattice: the spreading
+    radius of one row, a Laplace jump over the grid, and a probe of 1000
+    nodes."""
+    xs = np.arange(1000) % nx
+    ys = (np.arange(1000) * 7) % ny
+    calls = {"spreading_radius": lambda: lat.spreading_radius(25),
+             "laplace_jump": lambda: lat.laplace_jump(nx / 2, 120.0, 50.0, 150.0),
+             "probe_1000": lambda: lat.probe(xs, ys)}
+    out = {}
+    for name, fn in calls.items():
+        fn()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        out[name] = (time.perf_counter() - t0) / reps * 1e6
+    return out
 
 
 def run_ours(args):

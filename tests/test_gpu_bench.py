@@ -40,4 +40,8 @@ def test_bench_line_has_the_contract_keys():
     assert b["cases"] == 64 and b["value"] > 0 and b["sequential_fp32"] > 0 and b["batched_fp32"] > 0
     assert set(b["tile"]) == {"periodic", "walls"}
     assert d["clocks"] is None or "sm_mhz" in d["clocks"]
-    assert d["data_variants"]["perf-2048-drop"]["value"] > 0
+    v = d["data_variants"]
+    for k in ("perf-2048-drop", "perf-2048-eq29", "impact-2400x600-open-top"):
+        assert v[k]["value"] > 0 and v[k]["unit"] == "MLUPS", k
+    assert set(v["impact_tooling_us"]) == {"spreading_radius", "laplace_jump", "probe_1000"}
+    assert all(t > 0 for t in v["impact_tooling_us"].values())
