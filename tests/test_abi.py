@@ -146,3 +146,21 @@ def test_missing_library_fails_loudly(tmp_path):
         "    sys.exit(1)\n"
         "sys.exit(2 if 'oracle' in sys.modules else 0)\n")
     assert subprocess.run([sys.executable, "-c", code], cwd=str(tmp_path)).returncode == 0
+
+
+def test_batch_calls_check_their_arguments_on_the_host(L):
+    """lbm_batch_create rejects a missing output, a case count outside
+    1..200, a missing case array and a NULL case before any device work; the
+    other batch calls reject a NULL batch."""
+    out = ctypes.c_void_p(1)
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert L.lbm_batch_create(1, arr, None) == lbm.LBM_ERR_INVALID
+    for n, cases_ in ((0, arr), (201, arr), (1, None), (2, arr)):
+        out.value = 1
+        assert L.lbm_batch_create(n, cases_, ctypes.byref(out)) == lbm.LBM_ERR_INVALID, n
+        assert not out.value
+    n = ctypes.c_int()
+    assert L.lbm_batch_step(None, 1) == lbm.LBM_ERR_INVALID
+    assert L.lbm_batch_info(None, 0, ctypes.byref(n), None, None, None, None) == lbm.LBM_ERR_INVALID
+    assert L.lbm_batch_last_error(None)
+    L.lbm_batch_destroy(None)
