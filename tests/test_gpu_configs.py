@@ -11,9 +11,9 @@ holds the 16-bit run to what such round-off-level perturbations do:
   FP32 vs FP16-shifted storage: the same pattern over the first 200 steps
   (the correlation of phi - 1/2), the liquid fraction, and the domain length
   up to 20 000 steps within 2% of the envelope of three FP32 runs (two of
-  them perturbed).  Measured: the perturbed FP32 runs part by up to 4.6% in
+  them perturbed).  Measured: the perturbed FP32 runs part by up to 4.9% in
   domain length at ratio 1000 (0.7% at ratio 3) by 20 000 steps; FP16 runs lie
-  within 0.5% of the envelope.
+  inside the envelope or at most 1.3% outside it.
 * droplet impact, 2400 x 600 (D = 200, film 20, U = 0.04, We = 8000, ratio
   1000, mu ratio 40, W = 5, walls), Re = 20, 100, 500, FP32 vs BF16-shifted
   storage, the spreading radius every t* = 0.5 up to t* = 4.  FP32 is robust:
