@@ -196,6 +196,9 @@ class Lattice:
             pass
 
     def init(self, phi0, ux0=None, uy0=None, p0=None):
+        """Initial state from [ny, nx] fields: f = f^eq(phi0, u0) (Eq. 9),
+        g = g^eq(p0, rho(phi0), u0) (Eqs. 13, 16, 17), and the (phi u) history
+        phi0 u0, so d_t(phi u) starts at 0; u0 and p0 default to 0."""
         self._keep = [_f64(a) for a in (phi0, ux0, uy0, p0)]
         a = self._keep
         for x in a:
@@ -205,6 +208,8 @@ class Lattice:
         return self
 
     def step(self, nsteps: int = 1):
+        """nsteps time steps of Eqs. 8 and 15 with everything they use
+        (Sec. II), streaming with the lattice's boundary rule."""
         lib().orc_step(self._h, int(nsteps))
         return self
 
@@ -225,6 +230,7 @@ class Lattice:
                 buf[18 * N:].reshape(2, *s))
 
     def set_state(self, f, g, phiu):
+        """Load a pre-collision state in the layout get_state returns."""
         buf = np.concatenate([np.ravel(f), np.ravel(g), np.ravel(phiu)]).astype(np.float64)
         if buf.size != 20 * self.nx * self.ny:
             raise ValueError("state size mismatch")
@@ -232,4 +238,5 @@ class Lattice:
         return self
 
     def sum_phi(self) -> float:
+        """Sum of phi (Eq. 12) over the grid, a plain running sum."""
         return lib().orc_sum_phi(self._h)
