@@ -301,7 +301,7 @@ def run_batched(torch, lbm, stream, steps, storage=1):
         lat.close()
     bat = make(storage)
     b = lbm.Batch(bat)
-    b.step(100)                                   # tile-shape tuning + warm-up
+    b.step(150)                                   # tile-shape tuning (140 steps) + warm-up
     t_bat = _time_steps(torch, stream, lambda: b.step(steps))
     info = b.info()
     d_bat, u_bat = accuracy(bat)
@@ -311,7 +311,7 @@ def run_batched(torch, lbm, stream, steps, storage=1):
     # the same batch with FP32 storage: batching alone, at the plain path's precision
     bat32 = make(0)
     b32 = lbm.Batch(bat32)
-    b32.step(100)
+    b32.step(150)
     t_b32 = _time_steps(torch, stream, lambda: b32.step(steps))
     b32.close()
     for lat in bat32:

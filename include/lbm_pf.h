@@ -22,14 +22,22 @@
  *    are replaced by the row below's).
  *  - Host arrays passed in or out are double precision, N = nx*ny entries,
  *    owned by the caller; the library copies them and keeps no pointer.
- *  - All device memory is owned by the handle: allocated by lbm_create,
- *    released by lbm_destroy.  All GPU work is enqueued on params.stream
- *    (NULL = the legacy default stream).
+ *  - All device memory is owned by the handle: allocated by lbm_create
+ *    (stream-ordered, cudaMallocAsync on params.stream), released by
+ *    lbm_destroy (cudaFreeAsync, then a synchronisation of that stream);
+ *    lbm_create_in places it in a caller's buffer instead.  All GPU work is
+ *    enqueued on params.stream (NULL = the legacy default stream).
  *  - Every call returns an lbm_status; nothing aborts, traps or exits.  After
  *    a failure lbm_last_error(h) returns a one-line description.
  *  - A handle is not thread-safe: one host thread per handle.
- *  - Arithmetic on the device is IEEE FP32 (no fast-math); diagnostics that
- *    sum over the grid accumulate in FP64.
+ *  - Arithmetic on the device is FP32 (no fast-math): every addition,
+ *    multiplication and fused multiply-add is an explicit IEEE
+ *    round-to-nearest operation.  The step has no division or square root;
+ *    its five reciprocals, 1/rho (Eq. 22a), 1/tau_g (Eq. 23), the 1/nu
+ *    inversion of Eq. 25, 1/|grad phi| (Eq. 2) and 1/|C| (Eq. 29), use the
+ *    hardware approximations rcp.approx / rsqrt.approx (relative error below
+ *    2^-22, deterministic).  Diagnostics that sum over the grid accumulate in
+ *    FP64.
  */
 #ifndef LBM_PF_H
 #define LBM_PF_H
@@ -200,15 +208,23 @@ lbm_status lbm_diag(lbm_handle* h, double* sum_phi, double* umax, double* pmin,
  *             returns after enqueueing, d_out is ready when the stream is.
  *   err, err_len  optional host buffer for a one-line error message.
  * The block partials live in a fixed 128 KiB array inside the library image,
- * which every GPU that loads the library holds until the process exits.  The
- * first call on each device looks up that array's device address (with the
- * device current); make that first call before any stream capture.  All calls
- * on a device share the array: calls whose kernels overlap on the GPU (on
- * different streams, or from different threads) race and must be ordered by
- * the caller.  The array keeps the previous call's partials; each call
- * rewrites every slot it reads, so nothing needs clearing.  Errors:
- * LBM_ERR_INVALID (NULL pointer, n too large), LBM_ERR_CUDA (no device,
- * symbol lookup or launch failure).
+ * which every GPU that loads the library holds until the process exits.
+ * Set-up: the first call on each device, and the first call after that
+ * device was reset (cudaDeviceReset makes a new primary context), looks up
+ * the array's device address with the device current and loads the call's
+ * two kernels.  Under lazy module loading (the CUDA default) that set-up can
+ * load the library's device code, which allocates device memory for it and
+ * may synchronise: exactly what these callers avoid.  So make one warm-up
+ * call (n = 0 and any 4-double d_out will do) during your own set-up, before
+ * a memory pool takes over the device or a stream capture begins; later
+ * calls allocate nothing.  All calls on a device share the array: calls
+ * whose kernels overlap on the GPU (on different streams, or from different
+ * threads) race and must be ordered by the caller.  The array keeps the
+ * previous call's partials; each call rewrites every slot it reads, so
+ * nothing needs clearing.  Errors: LBM_ERR_INVALID (NULL pointer, n too
+ * large), LBM_ERR_CUDA (no device, a CUDA error already pending from earlier
+ * work -- reported and left pending, nothing launched --, set-up or launch
+ * failure).
  */
 lbm_status lbm_diag_fields_noalloc(const double* d_fields, size_t n, double* d_out, void* stream,
                                    char* err, size_t err_len);
@@ -233,15 +249,20 @@ lbm_status lbm_diag_fields_noalloc(const double* d_fields, size_t n, double* d_o
  *   own stream, and one launch per step covers the tiles of all its cases.  The
  *   two classes share no data, so their launch chains run concurrently.  Steps
  *   run as replays of a CUDA graph of 32 steps per class.  The first call with
- *   nsteps >= 100 times five tile shapes (32x4, 32x8, 32x16, 64x2, 64x4 nodes)
- *   for each class on its own first 100 steps and keeps the fastest.
+ *   nsteps >= 140 times five tile shapes (32x4, 32x8, 32x16, 64x2, 64x4 nodes)
+ *   for each class on its own first 140 steps (per shape 4 warm-up steps and
+ *   the faster of two windows of 12) and keeps the fastest.
  *   Ordered after earlier work on the cases' stream, and later work on that
  *   stream waits for it.  A case may also be stepped on its own between batch
  *   steps.  If any case was created with check_every > 0, the call ends by
  *   synchronising and returns LBM_ERR_NONFINITE (the first such case named by
  *   lbm_batch_last_error) when a case with check_every > 0 produced a
  *   non-finite phi, u or p during the call; all cases' flags are cleared.
- *   Otherwise the call is asynchronous.
+ *   Otherwise the call is asynchronous.  If a CUDA call fails after work was
+ *   enqueued (LBM_ERR_CUDA), the call orders the cases' stream after what was
+ *   enqueued and marks the batch and every case as failed: the cases answer
+ *   LBM_ERR_STATE until lbm_init or lbm_set_state restores them, and the
+ *   batch answers LBM_ERR_STATE to every further step (build a new one).
  * lbm_batch_info -- for class cls (0: periodic cases, 1: walled cases): the
  *   number of cases, the tile shape in use, its measured microseconds per
  *   step (0 before tuning or for an empty class) and whether tuning ran; any

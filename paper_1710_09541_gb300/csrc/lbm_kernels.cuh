@@ -115,12 +115,15 @@ __device__ __forceinline__ void pull9(const float* __restrict__ s, size_t Nz, co
 // through these, so no multiply-add contraction is left to the compiler and
 // every kernel that inlines the functions below (direct-load, TMA-staged,
 // field read-back, initialisation) produces the same bits for the same
-// inputs.  IEEE division and square root throughout.
+// inputs.  Additions, multiplications and fused multiply-adds are IEEE
+// round-to-nearest.  The step has no division or square root: the five
+// reciprocals it needs, 1/rho (Eq. 22a), 1/tau_g (Eq. 23), 1/(interpolated
+// 1/nu) (Eq. 25), 1/|grad phi| (Eq. 2) and 1/|C| (Eq. 29), use the hardware
+// approximations below.
 __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
 // Hardware reciprocal and reciprocal square root (one instruction each,
 // relative error below 2^-22; operands here are never subnormal: rho >= rho_g,
 // tau_g >= 1/2, |grad phi|^2 > 1e-12).  Deterministic, so every kernel still
@@ -134,6 +137,16 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// Record a non-finite node in the status flag with one atomic per warp: the
+// lowest lane of those that reach this call (the offending ones) reports for
+// all of them, so a blown-up state does not serialise on one address.
+__device__ __forceinline__ void report_nonfinite(unsigned int* flag) {
+    const unsigned int lanes = __activemask();
+    unsigned int lane;
+    asm("mov.u32 %0, %%laneid;" : "=r"(lane));
+    if (lane == (unsigned int)(__ffs(lanes) - 1)) atomicOr(flag, 1u);
 }
 
 // c_i . v for the nine directions of Eq. 10; opposite directions get exactly

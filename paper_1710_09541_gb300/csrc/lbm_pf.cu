@@ -8,7 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <atomic>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -190,7 +190,7 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
         return;
     }
     // one test: a NaN or Inf in any of phi, u, p makes the sum non-finite
-    if (!isfinite(add(add(phi, M.ux), add(M.uy, M.p)))) atomicOr(flag, 1u);
+    if (!isfinite(add(add(phi, M.ux), add(M.uy, M.p)))) report_nonfinite(flag);
 
 #if !LBM_EARLY_PHIU
     const float2 prev = make_float2(phiu[n32], phiu[N32 + n32]);
@@ -586,17 +586,16 @@ static Model make_model(const lbm_params& p) {
     return m;
 }
 
+// The handle's own buffers are stream-ordered allocations on its stream
+// (cudaMallocAsync / cudaFreeAsync), so creating and destroying handles does
+// not synchronise the whole device.
 static void release(lbm_handle* h) {
     if (!h->owns_memory) return;  // a caller's workspace stays the caller's
-    for (int b = 0; b < 2; ++b) {
-        cudaFree(h->f[b]);
-        cudaFree(h->g[b]);
-    }
-    cudaFree(h->phiu);
-    cudaFree(h->staging);
-    cudaFree(h->red_part);
-    cudaFree(h->red_res);
-    cudaFree(h->flag);
+    void* bufs[9] = {h->f[0], h->f[1], h->g[0], h->g[1], h->phiu, h->staging, h->red_part,
+                     h->red_res, h->flag};
+    for (void* b : bufs)
+        if (b) cudaFreeAsync(b, h->stream);
+    cudaStreamSynchronize(h->stream);
 }
 
 static size_t f_bytes(int storage, size_t N) {
@@ -769,7 +768,7 @@ static lbm_status create_handle(int nx, int ny, const lbm_params* p, void* ws, l
         if (ws)
             *slot[k] = static_cast<char*>(ws) + L.offset[k];
         else
-            e = cudaMalloc(slot[k], L.size[k]);
+            e = cudaMallocAsync(slot[k], L.size[k], h->stream);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1026,10 +1025,17 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 
 static __device__ __align__(256) double g_noalloc_part[4 * NOALLOC_MAX_BLOCKS];
 
-// Host-side: the array's name is only a host stand-in, never a device
-// address.  Its device address is looked up once per device (with that device
-// current) and cached here.
-static std::atomic<void*> g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+// Host side: the array's name is only a host stand-in, never a device
+// address.  Its device address is looked up per device, with that device
+// current, and cached together with the identity of the context it was
+// looked up in: after a device reset the primary context (and with it the
+// library's module) is new, and the next call looks the address up again.
+struct NoallocSlot {
+    unsigned long long ctx_id = 0;  // 0: not set up
+    void* ptr = nullptr;
+};
+static NoallocSlot g_noalloc_slot[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mutex;
 
 static void noalloc_msg(char* err, size_t len, const char* fmt, ...) {
     if (!err || len == 0) return;
@@ -1037,6 +1043,33 @@ static void noalloc_msg(char* err, size_t len, const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(err, len, fmt, ap);
     va_end(ap);
+}
+
+// Unique identity of the calling thread's current context (0 when none is
+// current yet), through the driver entry points the runtime exposes, so the
+// library needs no link against libcuda.
+static cudaError_t current_context_id(unsigned long long* id) {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    *id = 0;
+    if (!get_current || !get_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000,
+                                                         cudaEnableDefault, &q1);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorSymbolNotFound;
+        get_current = (PFN_cuCtxGetCurrent_v4000)f1;
+        get_id = (PFN_cuCtxGetId_v12000)f2;
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+    if (!ctx) return cudaSuccess;
+    if (get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -1066,18 +1099,46 @@ extern "C" lbm_status lbm_diag_fields_noalloc(const double* d_fields, size_t n, 
                     cudaGetErrorString(e));
         return LBM_ERR_CUDA;
     }
-    // set-up on the first call on this device: find the array's device address
-    double* part = (double*)g_noalloc_ptr[dev].load(std::memory_order_acquire);
-    if (!part) {
-        void* ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_part);
-        if (e != cudaSuccess || !ptr) {
-            noalloc_msg(err, err_len, "lbm_diag_fields_noalloc: cudaGetSymbolAddress failed: %s",
-                        cudaGetErrorString(e));
-            return LBM_ERR_CUDA;
+    // an error left by earlier, unrelated work is reported as such and left
+    // pending for its owner
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        noalloc_msg(err, err_len,
+                    "lbm_diag_fields_noalloc: an earlier CUDA error is pending (%s); nothing launched",
+                    cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
+    double* part = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        NoallocSlot& slot = g_noalloc_slot[dev];
+        unsigned long long id = 0;
+        e = current_context_id(&id);
+        if (e == cudaSuccess && (id == 0 || id != slot.ctx_id || !slot.ptr)) {
+            // set-up, on the first call on this device and after a device
+            // reset: the array's device address in the current context, and
+            // both kernels loaded now (under lazy module loading a first
+            // launch would load them)
+            void* ptr = nullptr;
+            cudaFuncAttributes fa;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_part);
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_diag_partial);
+            if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_diag_final);
+            if (e == cudaSuccess) e = current_context_id(&id);
+            if (e == cudaSuccess && (!ptr || id == 0)) e = cudaErrorInvalidSymbol;
+            if (e == cudaSuccess) {
+                slot.ctx_id = id;
+                slot.ptr = ptr;
+            } else {
+                slot = NoallocSlot();
+            }
         }
-        g_noalloc_ptr[dev].store(ptr, std::memory_order_release);
-        part = (double*)ptr;
+        part = (double*)slot.ptr;
+    }
+    if (e != cudaSuccess) {
+        noalloc_msg(err, err_len, "lbm_diag_fields_noalloc: set-up of the static array failed: %s",
+                    cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
     }
     cudaStream_t s = (cudaStream_t)stream;
     // every slot the final pass reads is rewritten by this call's first pass
@@ -1166,7 +1227,11 @@ constexpr int BATCH_NCAND = 5;
 constexpr int BATCH_TX[BATCH_NCAND] = {32, 32, 32, 64, 64};
 constexpr int BATCH_TY[BATCH_NCAND] = {4, 8, 16, 2, 4};
 constexpr int BATCH_GRAPH_STEPS = 32;  // steps per graph replay (even)
-constexpr int BATCH_TUNE_WARM = 4, BATCH_TUNE_STEPS = 16;
+// per shape: warm-up steps, then timed windows of steps; the shape's time is
+// its fastest window (a single window let the choice between shapes within
+// 2-3% of each other vary from run to run)
+constexpr int BATCH_TUNE_WARM = 4, BATCH_TUNE_WINDOW = 12, BATCH_TUNE_WINDOWS = 2;
+constexpr int BATCH_TUNE_PER_SHAPE = BATCH_TUNE_WARM + BATCH_TUNE_WINDOW * BATCH_TUNE_WINDOWS;
 
 using BatchKernel = void (*)(BatchTable, const int2*, int);
 
@@ -1225,6 +1290,7 @@ struct lbm_batch {
     bool tuned = false;
     double tuned_us[BATCH_NCLASS][BATCH_NCAND] = {};
     cudaGraphExec_t graph = nullptr;
+    bool failed = false;  // a step call failed after enqueueing work (see batch_abort)
     long long node_count = 0;
     char err[512] = {0};
     BatchTable& tab(int cls, int k) { return table[cls * BATCH_NCAND + k]; }
@@ -1313,6 +1379,21 @@ static lbm_status batch_join(lbm_batch* b) {
     return LBM_OK;
 }
 
+// A failure after the class streams forked: some steps of this call may be
+// enqueued, so the cases' current buffers are unknown.  Join the class
+// streams, order the cases' stream after them, and mark the batch and its
+// cases as failed: each case needs lbm_init or lbm_set_state before further
+// use, and the batch rejects further steps.
+static lbm_status batch_abort(lbm_batch* b, lbm_status st) {
+    cudaEventRecord(b->ev_join, b->bs[1]);
+    cudaStreamWaitEvent(b->bs[0], b->ev_join, 0);
+    cudaEventRecord(b->ev_out, b->bs[0]);
+    cudaStreamWaitEvent(b->user, b->ev_out, 0);
+    for (lbm_handle* h : b->cases) h->inited = false;
+    b->failed = true;
+    return st;
+}
+
 // after an odd number of batch steps every case's current buffer flips
 static void batch_flip(lbm_batch* b, long long steps) {
     if (steps & 1)
@@ -1331,14 +1412,18 @@ static lbm_status batch_tune(lbm_batch* b, long long& done) {
         for (int k = 0; k < BATCH_NCAND; ++k) {
             for (int w = 0; w < BATCH_TUNE_WARM; ++w, ++s)
                 if ((st = batch_launch(b, cls, k, (int)(s & 1))) != LBM_OK) return st;
-            LBM_BCUDA(b, cudaEventRecord(b->t0, b->bs[cls]));
-            for (int w = 0; w < BATCH_TUNE_STEPS; ++w, ++s)
-                if ((st = batch_launch(b, cls, k, (int)(s & 1))) != LBM_OK) return st;
-            LBM_BCUDA(b, cudaEventRecord(b->t1, b->bs[cls]));
-            LBM_BCUDA(b, cudaEventSynchronize(b->t1));
-            float ms = 0.f;
-            LBM_BCUDA(b, cudaEventElapsedTime(&ms, b->t0, b->t1));
-            b->tuned_us[cls][k] = 1e3 * ms / BATCH_TUNE_STEPS;
+            double us = 1e300;
+            for (int win = 0; win < BATCH_TUNE_WINDOWS; ++win) {
+                LBM_BCUDA(b, cudaEventRecord(b->t0, b->bs[cls]));
+                for (int w = 0; w < BATCH_TUNE_WINDOW; ++w, ++s)
+                    if ((st = batch_launch(b, cls, k, (int)(s & 1))) != LBM_OK) return st;
+                LBM_BCUDA(b, cudaEventRecord(b->t1, b->bs[cls]));
+                LBM_BCUDA(b, cudaEventSynchronize(b->t1));
+                float ms = 0.f;
+                LBM_BCUDA(b, cudaEventElapsedTime(&ms, b->t0, b->t1));
+                if (1e3 * ms / BATCH_TUNE_WINDOW < us) us = 1e3 * ms / BATCH_TUNE_WINDOW;
+            }
+            b->tuned_us[cls][k] = us;
             if (b->tuned_us[cls][k] < best) {
                 best = b->tuned_us[cls][k];
                 b->cand[cls] = k;
@@ -1533,38 +1618,50 @@ lbm_status lbm_batch_info(const lbm_batch* b, int cls, int* ncases, int* tile_tx
 
 lbm_status lbm_batch_step(lbm_batch* b, int nsteps) {
     if (!b) return LBM_ERR_INVALID;
+    if (b->failed)
+        return bfail(b, LBM_ERR_STATE, "lbm_batch_step: an earlier step call failed; re-initialise "
+                                       "the cases and build a new batch");
     if (nsteps < 0) return bfail(b, LBM_ERR_INVALID, "lbm_batch_step: nsteps < 0");
     if (nsteps == 0) return LBM_OK;
+    for (int c = 0; c < b->ncases; ++c)
+        if (!b->cases[c]->inited)
+            return bfail(b, LBM_ERR_STATE, "lbm_batch_step: case %d is not initialised", c);
     LBM_BCUDA(b, cudaSetDevice(b->device));
     // order after earlier work on the cases' stream
     LBM_BCUDA(b, cudaEventRecord(b->ev_in, b->user));
     LBM_BCUDA(b, cudaStreamWaitEvent(b->bs[0], b->ev_in, 0));
     batch_sync_table(b);
     lbm_status st;
-    if ((st = batch_fork(b)) != LBM_OK) return st;
+    if ((st = batch_fork(b)) != LBM_OK) return batch_abort(b, st);
 
     long long done = 0;
     // tune on the first call long enough: it runs tune_steps real steps
-    const int tune_steps = BATCH_NCAND * (BATCH_TUNE_WARM + BATCH_TUNE_STEPS);
+    const int tune_steps = BATCH_NCAND * BATCH_TUNE_PER_SHAPE;
     if (!b->tuned && nsteps >= tune_steps)
-        if ((st = batch_tune(b, done)) != LBM_OK) return st;
+        if ((st = batch_tune(b, done)) != LBM_OK) return batch_abort(b, st);
     // an odd count so far: one more step so the graph starts at parity 0
     if ((done & 1) && done < nsteps) {
-        if ((st = batch_run(b, done, done + 1)) != LBM_OK) return st;
+        if ((st = batch_run(b, done, done + 1)) != LBM_OK) return batch_abort(b, st);
         ++done;
     }
-    if ((st = batch_join(b)) != LBM_OK) return st;
+    if ((st = batch_join(b)) != LBM_OK) return batch_abort(b, st);
     // whole graph replays (BATCH_GRAPH_STEPS steps each, parity returns to 0)
     const long long reps = (nsteps - done) / BATCH_GRAPH_STEPS;
     if (reps > 0) {
-        if (!b->graph && (st = batch_capture(b)) != LBM_OK) return st;
-        for (long long r = 0; r < reps; ++r) LBM_BCUDA(b, cudaGraphLaunch(b->graph, b->bs[0]));
+        if (!b->graph && (st = batch_capture(b)) != LBM_OK) return batch_abort(b, st);
+        for (long long r = 0; r < reps; ++r) {
+            const cudaError_t ce = cudaGraphLaunch(b->graph, b->bs[0]);
+            if (ce != cudaSuccess)
+                return batch_abort(b, bfail(b, LBM_ERR_CUDA, "cudaGraphLaunch: %s",
+                                            cudaGetErrorString(ce)));
+        }
     }
     // the remainder, with parities continuing from 0 after the replays
     if (done + reps * BATCH_GRAPH_STEPS < nsteps) {
-        if ((st = batch_fork(b)) != LBM_OK) return st;
-        if ((st = batch_run(b, done + reps * BATCH_GRAPH_STEPS, nsteps)) != LBM_OK) return st;
-        if ((st = batch_join(b)) != LBM_OK) return st;
+        if ((st = batch_fork(b)) != LBM_OK) return batch_abort(b, st);
+        if ((st = batch_run(b, done + reps * BATCH_GRAPH_STEPS, nsteps)) != LBM_OK)
+            return batch_abort(b, st);
+        if ((st = batch_join(b)) != LBM_OK) return batch_abort(b, st);
     }
     // cases' current buffers (and with them the tables) follow
     batch_flip(b, nsteps);

@@ -12,7 +12,9 @@
 // The copies fill coordinates outside the grid with zeros; tiles on a
 // periodic edge patch those halo entries from global memory after the copy.
 // Every mbarrier wait is bounded; a timeout sets bit 1 of the status flag and
-// the block returns after a bounded wait for its other copy in flight.
+// the block returns after one more bounded wait on each stage with a copy in
+// flight (the late one included).  A handle whose step reported a timeout
+// must be destroyed: its state is undefined.
 #pragma once
 #include <cuda.h>
 
@@ -167,10 +169,12 @@ __global__ void __launch_bounds__(NT, 1)
         const int s = k & 1;
         const bool got = mbar_wait_bounded(&bar[s], (k >> 1) & 1);
         if (__syncthreads_or(!got)) {
-            // a copy never completed: report, wait (bounded) for the other
-            // stage's copy if one is in flight, and leave
+            // a copy never completed: report, wait (bounded) once more for
+            // the late stage's own copy and for the other stage's copy if one
+            // is in flight, and leave
             if (tid == 0) {
                 atomicOr(flag, 2u);
+                mbar_wait_bounded(&bar[s], (k >> 1) & 1);
                 if (t + stride < ntiles) mbar_wait_bounded(&bar[s ^ 1], ((k + 1) >> 1) & 1);
             }
             return;
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(NT, 1)
             const Stencil stc = stencil(phi, sp[1], sp[-1], sp[PW], sp[-PW], sp[PW + 1], sp[PW - 1],
                                         sp[-PW - 1], sp[-PW + 1]);
             const Macro M = macroscopic(m, g, phi, stc.gx, stc.gy, stc.lap);
-            if (!isfinite(add(add(phi, M.ux), add(M.uy, M.p)))) atomicOr(flag, 1u);
+            if (!isfinite(add(add(phi, M.ux), add(M.uy, M.p)))) report_nonfinite(flag);
             const float2 prev = make_float2(U[ly * TX + lx], U[TX * TY + ly * TX + lx]);
             const float2 now = collide(m, f, g, phi, stc, M, prev);
             const size_t n = (size_t)y * nx + x;

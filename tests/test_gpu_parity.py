@@ -79,9 +79,21 @@ def _max3x3(a, walls):
     return out
 
 
-def _one_step_parity(lbm, nx, ny, P, state, R=None):
-    """Load the same FP32 state into GPU and oracle, step once, compare the
-    full state (f, g, phi u) and the fields."""
+# |grad phi| (or |C| for Eq. 29) below which both sides take n = 0: the GPU's
+# value differs from the oracle's by at most eps * sqrt(2), so below
+# G_LOW + eps * sqrt(2) < 1e-6 (the cut-off of both) neither turns n on.
+G_LOW = {False: 0.5e-6, True: 0.4e-6}
+G_HIGH = 2e-6    # above: both take the same branch, n turns by eps / |grad phi|
+
+
+def _one_step_setup(nx, ny, P, state):
+    """The oracle's side of a one-step comparison from an FP32 state: the
+    state as the GPU gets it, the oracle's state and fields after one step,
+    the per-node bound on post-streaming f, and the share of nodes in each
+    regime of the sharpening normal: "off" (both sides n = 0, held to the
+    plain rounding bound), "band" (|grad phi| within the rounding of the
+    cut-off: either branch, allowance 0.35 |lambda|), "on" (allowance
+    0.35 |lambda| eps / |grad phi|), and "ill" (allowance above 1e-5)."""
     st32 = [np.ascontiguousarray(a, dtype=np.float32) for a in state]
     st64 = [a.astype(np.float64) for a in st32]
     o = oracle.Lattice(nx, ny, **P).set_state(*st64)
@@ -89,7 +101,6 @@ def _one_step_parity(lbm, nx, ny, P, state, R=None):
     walls = P.get("bc_y", 0) in (1, 2)   # stencil rows clamp at a wall and at the open top
     gx, gy, _ = oracle.grad_lap(pre["phi"], bc_y=P.get("bc_y", 0))
     lam = np.abs(4 * pre["phi"] * (1 - pre["phi"]) / P["W"])
-    gmag = np.hypot(gx, gy)
     local = P.get("normal_scheme", 0) == 1
     if local:
         # Eq. 29 takes n from C = sum c_i (f_i - f_i^eq) + d_t(phi u)/2, a sum of
@@ -100,29 +111,47 @@ def _one_step_parity(lbm, nx, ny, P, state, R=None):
         neq = f - w[:, None, None] * pre["phi"] * (1 + 3 * cu)
         Cx = (cx[:, None, None] * neq).sum(0) + 0.5 * (pre["phi"] * pre["ux"] - st64[2][0])
         Cy = (cy[:, None, None] * neq).sum(0) + 0.5 * (pre["phi"] * pre["uy"] - st64[2][1])
-        gmag, eps, gate = np.hypot(Cx, Cy), 4e-7, 2e-6
+        gmag, eps = np.hypot(Cx, Cy), 4e-7
     else:
-        gmag, eps, gate = np.hypot(gx, gy), EPS_GRAD, 2e-6  # |n| cut-off is 1e-6
-    cond = np.where(gmag < gate, 1.0, np.minimum(1.0, eps / np.maximum(gmag, 1e-300)))
+        gmag, eps = np.hypot(gx, gy), EPS_GRAD
+    lo = G_LOW[local]
+    cond = np.where(gmag < lo, 0.0,
+                    np.where(gmag < G_HIGH, 1.0, np.minimum(1.0, eps / np.maximum(gmag, 1e-300))))
     bound_f = 3e-7 + _max3x3(0.35 * lam * cond, walls)
     o.step(1)
-    of, og, ophiu = o.get_state()
-    with lbm.Lattice(nx, ny, **P) as g:
-        g.set_state(*st32).step(1)
-        gf, gg, gphiu = g.get_state()
-        got = g.fields()
-    ref = o.fields()
+    regimes = {"off": float((gmag < lo).mean()),
+               "band": float(((gmag >= lo) & (gmag < G_HIGH)).mean()),
+               "on": float((gmag >= G_HIGH).mean()),
+               "ill": float((0.35 * lam * cond > 1e-5).mean())}
+    return dict(st32=st32, ref_state=o.get_state(), ref=o.fields(), bound_f=bound_f, walls=walls,
+                regimes=regimes, shape=(nx, ny))
+
+
+def _one_step_check(S, got_state, got):
+    """The GPU's state and fields after the step against the oracle's."""
+    gf, gg, gphiu = got_state
+    of, og, ophiu = S["ref_state"]
+    ref, bound_f = S["ref"], S["bound_f"]
     assert np.all(np.abs(gf - of) <= bound_f[None]), float(np.abs(gf - of).max())
     assert np.abs(gg - og).max() <= 5e-6 * np.abs(og).max() + 1e-12
     # u carries the FP32 error of F = mu grad phi divided by rho (Eq. 22a)
     assert np.abs(gphiu - ophiu).max() <= 5e-6 * np.abs(ophiu).max() + 1e-8
-    ill = float((0.35 * lam * cond > 1e-5).mean())
-    sc = _scales(P, R)
     # fields of the new state: phi, rho, u within 2e-6 where n is well
     # conditioned everywhere; near ill-conditioned nodes phi inherits bound_f
-    phi_bound = 9 * _max3x3(bound_f, walls)
+    phi_bound = 9 * _max3x3(bound_f, S["walls"])
     assert np.all(np.abs(got["phi"] - ref["phi"]) <= phi_bound + 2e-6)
-    return ill
+    nx, ny = S["shape"]
+    print(f"one-step parity {nx}x{ny}: regimes {S['regimes']}")
+    return S["regimes"]
+
+
+def _one_step_parity(lbm, nx, ny, P, state, R=None):
+    """Load the same FP32 state into GPU and oracle, step once, compare the
+    full state (f, g, phi u) and the fields; returns the regime shares."""
+    S = _one_step_setup(nx, ny, P, state)
+    with lbm.Lattice(nx, ny, **P) as g:
+        g.set_state(*S["st32"]).step(1)
+        return _one_step_check(S, g.get_state(), g.fields())
 
 
 def _trajectory_states(nx, ny, P, phi0, u0=None, v0=None, T=300, every=50):
@@ -164,7 +193,7 @@ def test_one_step_parity_along_trajectory(lbm, name):
     nx, ny, P, init = TRAJ_CASES[name]
     ill = []
     for t, state in _trajectory_states(nx, ny, P, *init(), T=300, every=60):
-        ill.append(_one_step_parity(lbm, nx, ny, P, state))
+        ill.append(_one_step_parity(lbm, nx, ny, P, state)["ill"])
     # once the initial transient is over, ill-conditioned nodes are a minority
     assert ill[-1] < 0.05, ill
 
@@ -176,8 +205,8 @@ def test_one_step_parity_perf_2048(lbm):
     phi0, P = cases.perf_case()
     nx, ny = cases.PERF_NX, cases.PERF_NY
     o = oracle.Lattice(nx, ny, **P).init(phi0).step(3)
-    ill = _one_step_parity(lbm, nx, ny, P, o.get_state())
-    assert ill < 0.05
+    reg = _one_step_parity(lbm, nx, ny, P, o.get_state())
+    assert reg["ill"] < 0.05
 
 
 def test_one_step_parity_impact_2400x600(lbm):
