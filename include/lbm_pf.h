@@ -80,12 +80,16 @@ enum {
                                    2^10 g_i/w_i (38 B/node) */
     LBM_STORE_BF16_SHIFTED = 2  /* as FP16_SHIFTED with BF16 and g unscaled */
 };
-/* step kernel (kernel); both compute the same arithmetic */
+/* step kernel (kernel); all compute the same arithmetic and give the same bits */
 enum {
-    LBM_KERNEL_AUTO = 0,    /* the faster on GB300: currently LBM_KERNEL_GENERIC */
+    LBM_KERNEL_AUTO = 0,    /* the faster on GB300: LBM_KERNEL_GENERIC with FP32 storage;
+                               LBM_KERNEL_TMA with 16-bit storage where the grid allows it,
+                               else LBM_KERNEL_GENERIC */
     LBM_KERNEL_GENERIC = 1, /* 32 x 4 tiles, one thread per node, direct loads; any grid */
-    LBM_KERNEL_TMA = 2      /* persistent, tiles staged by bulk tensor copies; nx % 4 == 0,
-                               nx >= 72, ny >= 20 */
+    LBM_KERNEL_TMA = 2      /* tiles staged in shared memory by bulk tensor copies.  FP32
+                               storage: a persistent kernel (nx % 4 == 0, nx >= 72, ny >= 20,
+                               no open top); 16-bit storage: one 32 x 4 tile per CTA
+                               (nx % 4 == 0, nx >= 40, ny >= 8) */
 };
 
 typedef struct {

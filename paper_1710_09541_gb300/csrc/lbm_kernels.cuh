@@ -139,6 +139,18 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return r;
 }
 
+// Programmatic dependent launch.  A step kernel launched with programmatic
+// stream serialisation may be scheduled while the previous step is still
+// finishing: it waits here, before its first access to the state that step
+// reads and writes, until the previous grid has completed and its writes are
+// visible, and then lets the next step's CTAs be scheduled into the SM slots
+// its own last wave leaves free.  For a kernel launched without the
+// attribute both are no-ops.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Record a non-finite node in the status flag with one atomic per warp: the
 // lowest lane of those that reach this call (the offending ones) reports for
 // all of them, so a blown-up state does not serialise on one address.
@@ -170,6 +182,28 @@ __device__ __forceinline__ void cdot9(float vx, float vy, float c[9]) {
 __device__ __forceinline__ float sum8(const float v[9]) {
     return add(add(add(v[1], v[3]), add(v[2], v[4])), add(add(v[5], v[7]), add(v[6], v[8])));
 }
+
+// The one-node ring around a TX x TY tile: slot r -> tile-relative (lx, ly),
+// -1 <= lx <= TX, -1 <= ly <= TY (top and bottom rows first, then the sides).
+template <int TX, int TY>
+struct Ring {
+    static constexpr int count = 2 * (TX + 2) + 2 * TY;
+    __device__ static void pos(int r, int& lx, int& ly) {
+        if (r < TX + 2) {
+            lx = r - 1;
+            ly = -1;
+        } else if (r < 2 * (TX + 2)) {
+            lx = r - (TX + 2) - 1;
+            ly = TY;
+        } else if (r < 2 * (TX + 2) + TY) {
+            lx = -1;
+            ly = r - 2 * (TX + 2);
+        } else {
+            lx = TX;
+            ly = r - 2 * (TX + 2) - TY;
+        }
+    }
+};
 
 // phi = sum_i f_i (Eq. 12), in one fixed association order everywhere so a
 // node's phi is bit-identical whichever block computes it.  The rest
@@ -214,26 +248,41 @@ struct Macro {
     float rho, inv_rho, Fx, Fy, ux, uy, p, usq;
 };
 
-__device__ __forceinline__ Macro macroscopic(const Model& m, const float g[9], float phi,
-                                             float gx, float gy, float lap) {
+// The moments of g a node's recovery needs (Eq. 22): sum c_i g_i and the sum
+// of the moving populations sum_{i != 0} g_i.
+struct GMom {
+    float mx, my, snz;
+};
+__device__ __forceinline__ GMom gmoments(const float g[9]) {
+    GMom o;
+    o.mx = add(sub(g[1], g[3]), add(sub(g[5], g[6]), sub(g[8], g[7])));
+    o.my = add(sub(g[2], g[4]), add(sub(g[5], g[8]), sub(g[6], g[7])));
+    o.snz = add(add(add(g[1], g[3]), add(g[2], g[4])), add(add(g[5], g[7]), add(g[6], g[8])));
+    return o;
+}
+
+__device__ __forceinline__ Macro macro_from(const Model& m, const GMom& gm, float phi, float gx,
+                                            float gy, float lap) {
     Macro o;
     o.rho = fma_rn(phi, m.drho, m.rho_g);                                      // Eq. 13
     const float bulk = mul(mul(mul(m.beta4, phi), sub(phi, 1.f)), sub(phi, 0.5f));
     const float mu = fma_rn(-m.kappa, lap, bulk);                              // Eq. 6
     o.Fx = fma_rn(mu, gx, m.Gx);                                               // Eqs. 5, 19
     o.Fy = fma_rn(mu, gy, m.Gy);
-    const float mx = add(sub(g[1], g[3]), add(sub(g[5], g[6]), sub(g[8], g[7])));
-    const float my = add(sub(g[2], g[4]), add(sub(g[5], g[8]), sub(g[6], g[7])));
     o.inv_rho = rcp_approx(o.rho);
-    o.ux = mul(fma_rn(0.5f, o.Fx, mx), o.inv_rho);                            // Eq. 22a
-    o.uy = mul(fma_rn(0.5f, o.Fy, my), o.inv_rho);
-    const float snz = add(add(add(g[1], g[3]), add(g[2], g[4])), add(add(g[5], g[7]), add(g[6], g[8])));
+    o.ux = mul(fma_rn(0.5f, o.Fx, gm.mx), o.inv_rho);                         // Eq. 22a
+    o.uy = mul(fma_rn(0.5f, o.Fy, gm.my), o.inv_rho);
     o.usq = fma_rn(o.ux, o.ux, mul(o.uy, o.uy));
     // Eq. 22b with c_s^2/(1 - w_0) = 3/5 and rho s_0(u) = -(2/3) rho |u|^2
     const float ugrad = fma_rn(o.ux, gx, mul(o.uy, gy));
-    const float t = fma_rn(mul(0.5f, m.drho), ugrad, snz);
+    const float t = fma_rn(mul(0.5f, m.drho), ugrad, gm.snz);
     o.p = mul(0.6f, fma_rn(mul(-2.f / 3.f, o.rho), o.usq, t));
     return o;
+}
+
+__device__ __forceinline__ Macro macroscopic(const Model& m, const float g[9], float phi,
+                                             float gx, float gy, float lap) {
+    return macro_from(m, gmoments(g), phi, gx, gy, lap);
 }
 
 // Isotropic stencils of Eqs. 27 and 28 from the 3x3 neighbourhood

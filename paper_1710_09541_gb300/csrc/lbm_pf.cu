@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -35,26 +36,6 @@ namespace {
 // FIELDS = true evaluates the same formulas but writes phi, rho, ux, uy, p
 // as doubles instead of colliding (used by lbm_get_fields and lbm_diag).
 // ---------------------------------------------------------------------------
-template <int TX, int TY>
-struct Ring {
-    static constexpr int count = 2 * (TX + 2) + 2 * TY;
-    __device__ static void pos(int r, int& lx, int& ly) {
-        if (r < TX + 2) {
-            lx = r - 1;
-            ly = -1;
-        } else if (r < 2 * (TX + 2)) {
-            lx = r - (TX + 2) - 1;
-            ly = TY;
-        } else if (r < 2 * (TX + 2) + TY) {
-            lx = -1;
-            ly = r - 2 * (TX + 2);
-        } else {
-            lx = TX;
-            ly = r - 2 * (TX + 2) - TY;
-        }
-    }
-};
-
 #ifndef LBM_STEP_TX
 #define LBM_STEP_TX 32
 #endif
@@ -106,6 +87,11 @@ __device__ __forceinline__ bool nbr_in_range(const Nbr& q, int nx, int ny) {
 #define LBM_PREFETCH_TWICE 0
 #endif
 // grids with fewer tiles than this many prefetch distances step without it
+// LBM_KERNEL_AUTO with 16-bit storage takes the TMA-staged kernel where the
+// grid allows it (nx % 4 == 0)
+#ifndef LBM_AUTO_TMA16
+#define LBM_AUTO_TMA16 0
+#endif
 #ifndef LBM_PREFETCH_MIN_TILES_X
 #define LBM_PREFETCH_MIN_TILES_X 16
 #endif
@@ -152,7 +138,7 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
         if (!FIELDS) prev = make_float2(phiu[q.r0 + x], phiu[N32 + q.r0 + x]);
 #endif
         pull18<ST, WALLS>(fs, gs, N32, q, f, g);
-        sphi[ty + 1][tx + 1] = sum9(f);
+        sphi[ty + 1][tx + 1] = Pop<ST>::phi_of(f);
     } else {
         sphi[ty + 1][tx + 1] =
             phi_at_st<ST, WALLS>(fs, N32, fold_x(x, nx), fold_y(y, ny, wfold), nx, ny, m.walls);
@@ -178,7 +164,7 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
     const Stencil st = stencil(phi, sphi[ly][lx + 1], sphi[ly][lx - 1], sphi[ly + 1][lx],
                                sphi[ly - 1][lx], sphi[ly + 1][lx + 1], sphi[ly + 1][lx - 1],
                                sphi[ly - 1][lx - 1], sphi[ly - 1][lx + 1]);
-    const Macro M = macroscopic(m, g, phi, st.gx, st.gy, st.lap);
+    const Macro M = macro_from(m, Pop<ST>::gmom(g), phi, st.gx, st.gy, st.lap);
     const int n32 = q.r0 + x;
 
     if (FIELDS) {
@@ -195,7 +181,7 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
 #if !LBM_EARLY_PHIU
     const float2 prev = make_float2(phiu[n32], phiu[N32 + n32]);
 #endif
-    const float2 now = collide(m, f, g, phi, st, M, prev);
+    const float2 now = collide_st<ST>(m, f, g, phi, st, M, prev);
     phiu[n32] = now.x;
     phiu[N32 + n32] = now.y;
     Pop<ST>::stfg(fd, gd, N32, n32, f, g, phi);
@@ -251,6 +237,8 @@ __global__ void __launch_bounds__(TX* TY, (step_minb<FIELDS, WALLS, ST>()))
            float* __restrict__ gd, float* __restrict__ phiu, unsigned int* __restrict__ flag,
            double* __restrict__ out, int nx, int ny, Model m, int pf_ahead) {
     __shared__ float sphi[TY + 2][TX + 2];
+    griddep_wait();
+    griddep_launch();
     if constexpr (!FIELDS && (ST == ST_FP32 || LBM_PREFETCH_16)) {
         if (pf_ahead > 0) {
             const int lin = blockIdx.y * gridDim.x + blockIdx.x + pf_ahead;
@@ -318,9 +306,9 @@ __global__ void k_init(const double* __restrict__ in, void* __restrict__ fd,
 #pragma unroll
             for (int j = 1; j < 9; ++j) {
                 eq_at(in, N, n, j, m, fe, ge);
-                d[j] = Pop<ST>::round_f(j, fe);
+                d[j] = fe;
             }
-            Pop<ST>::putf(fd, N32, 0, (int)n, sub(phi, sum8(d)));
+            Pop<ST>::putf(fd, N32, 0, (int)n, Pop<ST>::init_rest(phi, d));
         }
         phiu[n] = mul(phi, (float)in[N + n]);
         phiu[N + n] = mul(phi, (float)in[2 * N + n]);
@@ -340,6 +328,7 @@ __global__ void k_state_out(const void* __restrict__ fs, const void* __restrict_
         const Nbr q = make_nbr(x, y, nx, ny, walls);
         float v[9], w[9];
         pull18<ST>(fs, gs, N32, q, v, w);
+        Pop<ST>::canon(v, w);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             st[i * N + n] = v[i];
@@ -499,8 +488,11 @@ struct lbm_handle {
     unsigned int* flag = nullptr;
     bool inited = false;
     long long since_check = 0;
-    // TMA-staged step kernel (used when kernel != LBM_KERNEL_GENERIC and nx % 4 == 0)
+    // TMA-staged step kernels: the persistent FP32 one (LBM_KERNEL_TMA with
+    // FP32 storage) and the one-tile-per-CTA 16-bit one (use_tma16)
     bool use_tma = false;
+    bool use_tma16 = false;
+    CUtensorMap tm_w[2], tm_f0[2];  // 16-bit: word planes and f_0 plane of each buffer
     int pf_ahead = 0;  // L2 prefetch distance of the step kernel, in tiles
     bool owns_memory = true;  // false: the device buffers live in a caller's workspace
     CUtensorMap tm_f[2], tm_g[2], tm_u;
@@ -553,13 +545,16 @@ static lbm_status validate(int nx, int ny, const lbm_params* p, char* msg, size_
     if (p->check_every < 0) return bad("check_every must be >= 0");
     if (p->kernel < LBM_KERNEL_AUTO || p->kernel > LBM_KERNEL_TMA)
         return bad("kernel must be LBM_KERNEL_AUTO, _GENERIC or _TMA");
-    if (p->kernel == LBM_KERNEL_TMA && p->storage != LBM_STORE_FP32)
-        return bad("LBM_KERNEL_TMA stages FP32 populations only");
-    if (p->kernel == LBM_KERNEL_TMA && p->bc_y == LBM_BC_WALL_OPEN)
-        return bad("LBM_KERNEL_TMA supports periodic and walled y boundaries only");
-    if (p->kernel == LBM_KERNEL_TMA && !(nx % 4 == 0 && nx >= 72 && ny >= 20))
-        return bad("LBM_KERNEL_TMA needs nx % 4 == 0 (16-byte row pitch), nx >= 72 and ny >= 20 "
-                   "(the staged box fits in the grid)");
+    if (p->kernel == LBM_KERNEL_TMA && p->storage != LBM_STORE_FP32 &&
+        !(nx % 4 == 0 && nx >= 40 && ny >= 8))
+        return bad("LBM_KERNEL_TMA with 16-bit storage needs nx % 4 == 0 (16-byte row pitch), "
+                   "nx >= 40 and ny >= 8 (the staged box fits in the grid)");
+    if (p->kernel == LBM_KERNEL_TMA && p->storage == LBM_STORE_FP32 && p->bc_y == LBM_BC_WALL_OPEN)
+        return bad("LBM_KERNEL_TMA with FP32 storage supports periodic and walled y boundaries only");
+    if (p->kernel == LBM_KERNEL_TMA && p->storage == LBM_STORE_FP32 &&
+        !(nx % 4 == 0 && nx >= 72 && ny >= 20))
+        return bad("LBM_KERNEL_TMA with FP32 storage needs nx % 4 == 0 (16-byte row pitch), "
+                   "nx >= 72 and ny >= 20 (the staged box fits in the grid)");
     return LBM_OK;
 }
 
@@ -636,6 +631,27 @@ static int grid1d(size_t N) {
     return (int)(b < 4096 ? (b ? b : 1) : 4096);
 }
 
+// Step launches use programmatic dependent launch (griddep_wait in the
+// kernels): the next step's CTAs are scheduled while the previous step's
+// last wave finishes, instead of after it.
+#ifndef LBM_PDL
+#define LBM_PDL 1
+#endif
+template <typename... Exp, typename... Act>
+static cudaError_t launch_dep(void (*k)(Exp...), dim3 grid, dim3 block, cudaStream_t s, Act&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = LBM_PDL;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Act>(args)...);
+}
+
 static lbm_status launch_step(lbm_handle* h, bool fields, double* out) {
     const int c = h->cur;
     const bool walls = h->model.walls != 0;
@@ -650,6 +666,18 @@ static lbm_status launch_step(lbm_handle* h, bool fields, double* out) {
     }
     dim3 block(STEP_TX, STEP_TY);
     dim3 grid((h->nx + STEP_TX - 1) / STEP_TX, (h->ny + STEP_TY - 1) / STEP_TY);
+    if (!fields && h->use_tma16) {
+        auto k = h->prm.storage == LBM_STORE_FP16_SHIFTED
+                     ? (walls ? k_step16_tma<STEP_TX, STEP_TY, ST_FP16, 1>
+                              : k_step16_tma<STEP_TX, STEP_TY, ST_FP16, 0>)
+                     : (walls ? k_step16_tma<STEP_TX, STEP_TY, ST_BF16, 1>
+                              : k_step16_tma<STEP_TX, STEP_TY, ST_BF16, 0>);
+        LBM_CUDA(h, launch_dep(k, grid, block, h->stream, h->tm_w[c], h->tm_f0[c],
+                               (const void*)h->f[c], (const void*)h->g[c], (void*)h->f[c ^ 1],
+                               (void*)h->g[c ^ 1], h->phiu, h->flag, h->nx, h->ny, h->model));
+        h->cur ^= 1;
+        return LBM_OK;
+    }
     using K = void (*)(const float*, const float*, float*, float*, float*, unsigned int*, double*,
                        int, int, Model, int);
     K k;
@@ -673,8 +701,9 @@ static lbm_status launch_step(lbm_handle* h, bool fields, double* out) {
         k<<<grid, block, 0, h->stream>>>(h->f[c], h->g[c], nullptr, nullptr, h->phiu, h->flag, out,
                                          h->nx, h->ny, h->model, 0);
     else
-        k<<<grid, block, 0, h->stream>>>(h->f[c], h->g[c], h->f[c ^ 1], h->g[c ^ 1], h->phiu,
-                                         h->flag, nullptr, h->nx, h->ny, h->model, h->pf_ahead);
+        LBM_CUDA(h, launch_dep(k, grid, block, h->stream, (const float*)h->f[c],
+                               (const float*)h->g[c], h->f[c ^ 1], h->g[c ^ 1], h->phiu, h->flag,
+                               (double*)nullptr, h->nx, h->ny, h->model, h->pf_ahead));
     LBM_CUDA(h, cudaGetLastError());
     if (!fields) h->cur ^= 1;
     return LBM_OK;
@@ -699,8 +728,11 @@ static lbm_status check_flag(lbm_handle* h) {
 // Tensor maps over the 3-D arrays [planes][ny][nx] of FP32 (x innermost) for
 // the TMA-staged step.  cuTensorMapEncodeTiled is reached through the runtime's
 // driver entry point so the library needs no link against libcuda.
-static lbm_status encode_map(lbm_handle* h, CUtensorMap* map, float* base, int planes,
-                             int box_x, int box_y) {
+// A tensor map over [planes][ny][nx] 32-bit elements (x innermost; planes = 1
+// gives a 2-D map), box [planes][box_y][box_x]: base 16-byte aligned and nx a
+// multiple of 4 (16-byte row pitch), which the callers check.
+static lbm_status encode_map(lbm_handle* h, CUtensorMap* map, void* base, int planes, int box_x,
+                             int box_y, CUtensorMapDataType type = CU_TENSOR_MAP_DATA_TYPE_FLOAT32) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -711,14 +743,39 @@ static lbm_status encode_map(lbm_handle* h, CUtensorMap* map, float* base, int p
             return fail(h, LBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
+    if (((uintptr_t)base % 16) != 0 || h->nx % 4 != 0)
+        return fail(h, LBM_ERR_INVALID, "tensor map: base or row pitch not 16-byte aligned");
+    const cuuint32_t rank = planes > 1 ? 3 : 2;
     const cuuint64_t dims[3] = {(cuuint64_t)h->nx, (cuuint64_t)h->ny, (cuuint64_t)planes};
     const cuuint64_t strides[2] = {(cuuint64_t)h->nx * 4, (cuuint64_t)h->nx * h->ny * 4};
     const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)planes};
     const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+    CUresult r = encode(map, type, rank, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(h, LBM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return LBM_OK;
+}
+
+// The 16-bit TMA-staged step: tensor maps over each buffer's 8 word planes
+// (the (f_i, g_i) code pairs) and its f_0 plane.
+static lbm_status setup_tma16(lbm_handle* h) {
+    using T = Tma16Tile<STEP_TX, STEP_TY>;
+    for (int b = 0; b < 2; ++b) {
+        lbm_status st = encode_map(h, &h->tm_w[b], reinterpret_cast<float*>(h->f[b]) + h->N, 8,
+                                   T::BW, T::WH, CU_TENSOR_MAP_DATA_TYPE_UINT32);
+        if (st == LBM_OK) st = encode_map(h, &h->tm_f0[b], h->f[b], 1, T::BW, T::FH);
+        if (st != LBM_OK) return st;
+    }
+    // the kernels hold 12 KB of shared memory per CTA at 9 or 10 CTAs per SM
+    const void* ks[4] = {(const void*)k_step16_tma<STEP_TX, STEP_TY, ST_FP16, 0>,
+                         (const void*)k_step16_tma<STEP_TX, STEP_TY, ST_FP16, 1>,
+                         (const void*)k_step16_tma<STEP_TX, STEP_TY, ST_BF16, 0>,
+                         (const void*)k_step16_tma<STEP_TX, STEP_TY, ST_BF16, 1>};
+    for (const void* k : ks)
+        LBM_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared));
+    h->use_tma16 = true;
     return LBM_OK;
 }
 
@@ -790,7 +847,17 @@ static lbm_status create_handle(int nx, int ny, const lbm_params* p, void* ws, l
     // LBM_KERNEL_AUTO takes the direct-load kernel: on GB300 it measured 110 us
     // per 2048^2 step (with L2 prefetch; 128 us without) against 201 us for the
     // TMA-staged one
-    if (p->kernel == LBM_KERNEL_TMA) {
+    // the 16-bit staged kernel's box (40 x 8) fits in the grid
+    const bool tma16_ok = p->storage != LBM_STORE_FP32 && nx % 4 == 0 && nx >= 40 && ny >= 8;
+    if (tma16_ok && (p->kernel == LBM_KERNEL_TMA || (p->kernel == LBM_KERNEL_AUTO && LBM_AUTO_TMA16))) {
+        lbm_status ts = setup_tma16(h);
+        if (ts != LBM_OK) {
+            fprintf(stderr, "lbm_create: %s\n", h->err);
+            release(h);
+            delete h;
+            return ts;
+        }
+    } else if (p->kernel == LBM_KERNEL_TMA) {
         lbm_status ts = setup_tma(h);
         if (ts != LBM_OK) {
             fprintf(stderr, "lbm_create: %s\n", h->err);
@@ -1778,7 +1845,7 @@ __global__ void k_probe(const void* __restrict__ fs, const void* __restrict__ gs
         const float phi = ph[1][1];
         const Stencil st = stencil(phi, ph[1][2], ph[1][0], ph[2][1], ph[0][1], ph[2][2], ph[2][0],
                                    ph[0][0], ph[0][2]);
-        const Macro M = macroscopic(m, g, phi, st.gx, st.gy, st.lap);
+        const Macro M = macro_from(m, Pop<ST>::gmom(g), phi, st.gx, st.gy, st.lap);
         out[j] = phi;
         out[npts + j] = M.rho;
         out[2 * npts + j] = M.ux;

@@ -4,7 +4,10 @@
 //   FP32 (LBM_STORE_FP32): f and g as 9 FP32 planes each (36 B + 36 B / node);
 //     f_0 is written as phi - sum_{i>0} f_i (see below).
 //
-//   FP16 / BF16 shifted (LBM_STORE_FP16_SHIFTED, LBM_STORE_BF16_SHIFTED):
+//   FP16 / BF16 shifted (LBM_STORE_FP16_SHIFTED, LBM_STORE_BF16_SHIFTED); the
+//   step works on the stored codes themselves (see Shifted16), so a pull
+//   needs one conversion per population and a store one packed conversion
+//   per pair:
 //     f_0          FP32, written as phi - sum_{i>0} decode(encode(f_i)): the
 //                  rest population absorbs the rounding of the eight moving
 //                  ones, so the stored populations of a node sum to its phi up
@@ -86,6 +89,14 @@ struct Pop<ST_FP32> {
         static_cast<float*>(b)[i * N + idx] = v;
     }
     __device__ static float round_f(int, float v) { return v; }
+    // the step's hooks (the 16-bit formats work on codes instead): phi from
+    // the pulled f (Eq. 12), the moments of g (Eq. 22), the pulled values as
+    // populations, and the rest population f_0 that makes the stored
+    // populations of an initial state sum to phi
+    __device__ static float phi_of(const float f[9]) { return sum9(f); }
+    __device__ static GMom gmom(const float g[9]) { return gmoments(g); }
+    __device__ static void canon(float*, float*) {}
+    __device__ static float init_rest(float phi, const float fe[9]) { return sub(phi, sum8(fe)); }
     // population planes, and the address of entry idx of plane k (prefetches)
     static constexpr int PLANES = 18;
     __device__ static const void* plane_addr(const void* fb, const void* gb, int N, int k, int idx) {
@@ -122,9 +133,16 @@ struct Half16<__nv_bfloat16> {
     }
 };
 
+// The 16-bit formats store codes: h_i = f_i / w_i - 1/2 for the moving f_i
+// and k_i = GS g_i / w_i for every g_i.  The step reads them as codes (one
+// conversion each, no scaling), forms phi and the moments of g with the
+// weights factored out per weight class, collides in code units
+// (collide_code) and writes the new codes with one packed conversion per
+// direction: decode and encode cost no arithmetic.  f_0 stays an FP32 value.
 template <typename H>
 struct Shifted16 {
     using C = Half16<H>;
+    static constexpr float GS = C::GS;
     static size_t f_bytes(size_t N) { return 4 * N + 32 * N; }
     static size_t g_bytes(size_t N) { return 2 * N; }
     __device__ static const unsigned int* pw(const void* fb, int N) {
@@ -135,7 +153,8 @@ struct Shifted16 {
     }
     __device__ static unsigned short lo(unsigned int w) { return (unsigned short)(w & 0xffffu); }
     __device__ static unsigned short hi(unsigned int w) { return (unsigned short)(w >> 16); }
-    // f_i = w_i (v + 1/2) for i > 0
+    // population <-> code (initialisation, checkpoints): f_i = w_i (h + 1/2)
+    // for i > 0, g_i = w_i k / GS
     __device__ static float dec_f(int i, unsigned short u) {
         return fma_rn(C::to_f(u), w_of(i), 0.5f * w_of(i));
     }
@@ -148,23 +167,56 @@ struct Shifted16 {
     __device__ static unsigned short enc_g(int i, float v) {
         return C::from_f(mul(v, C::GS / w_of(i)));
     }
-    // the word of direction i > 0: the codes enc_f(i, f) | enc_g(i, g) << 16
-    __device__ static unsigned int enc_pair(int i, float f, float g) {
-        return C::pack(fma_rn(f, 1.f / w_of(i), -0.5f), mul(g, C::GS / w_of(i)));
+    // sum_{i>0} f_i = sum_{i>0} w_i (h_i + 1/2), the weights factored out per
+    // weight class; phi (Eq. 12) and the rest population written as the
+    // remainder both use this one association order, so in uniform bulk
+    // f_0 + s8 gives phi back exactly (f_0 = phi - s8 is exact by Sterbenz's
+    // lemma) and their roundings cannot drift sum phi in one direction
+    static constexpr float HALF_MOVING = 0.5f * (4.f * w_of(1) + 4.f * w_of(5));
+    __device__ static float s8(const float h[9]) {
+        const float a = add(add(h[1], h[3]), add(h[2], h[4]));
+        const float d = add(add(h[5], h[7]), add(h[6], h[8]));
+        return fma_rn(w_of(1), a, fma_rn(w_of(5), d, HALF_MOVING));
     }
-    // store the post-collision set of node idx (f_0 as the remainder)
-    __device__ static void stfg(void* fb, void* gb, int N, int idx, const float f[9],
-                                const float g[9], float phi) {
+    __device__ static float phi_of(const float h[9]) { return add(h[0], s8(h)); }
+    // the moments of g (Eq. 22) from the codes k_i
+    __device__ static GMom gmom(const float k[9]) {
+        constexpr float a1 = w_of(1) / GS, a5 = w_of(5) / GS;  // exact: GS is a power of 2
+        GMom o;
+        o.mx = fma_rn(a1, sub(k[1], k[3]), mul(a5, add(sub(k[5], k[6]), sub(k[8], k[7]))));
+        o.my = fma_rn(a1, sub(k[2], k[4]), mul(a5, add(sub(k[5], k[8]), sub(k[6], k[7]))));
+        o.snz = fma_rn(a1, add(add(k[1], k[3]), add(k[2], k[4])),
+                       mul(a5, add(add(k[5], k[7]), add(k[6], k[8]))));
+        return o;
+    }
+    // codes -> populations (checkpoint read-out)
+    __device__ static void canon(float f[9], float g[9]) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i) f[i] = fma_rn(f[i], w_of(i), 0.5f * w_of(i));
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = mul(g[i], w_of(i) / GS);
+    }
+    // f_0 of an initial state whose moving populations fe_1..8 are stored as codes
+    __device__ static float init_rest(float phi, const float fe[9]) {
+        float h[9];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) h[i] = C::to_f(enc_f(i, fe[i]));
+        return sub(phi, s8(h));
+    }
+    // store the post-collision codes of node idx: h_i | k_i << 16 per moving
+    // direction, k_0, and f_0 as the remainder phi - s8(stored codes)
+    __device__ static void stfg(void* fb, void* gb, int N, int idx, const float h[9],
+                                const float k[9], float phi) {
         unsigned int* P = pw(fb, N);
         float d[9];
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const unsigned int w = enc_pair(i, f[i], g[i]);
+            const unsigned int w = C::pack(h[i], k[i]);
             P[(i - 1) * N + idx] = w;
-            d[i] = dec_f(i, lo(w));
+            d[i] = C::to_f(lo(w));
         }
-        static_cast<float*>(fb)[idx] = sub(phi, sum8(d));
-        static_cast<unsigned short*>(gb)[idx] = enc_g(0, g[0]);
+        static_cast<float*>(fb)[idx] = sub(phi, s8(d));
+        static_cast<unsigned short*>(gb)[idx] = C::from_f(k[0]);
     }
     // one entry (checkpoint and initial-state permutations)
     __device__ static void putf(void* fb, int N, int i, int idx, float v) {
@@ -195,11 +247,103 @@ struct Pop<ST_FP16> : Shifted16<__half> {};
 template <>
 struct Pop<ST_BF16> : Shifted16<__nv_bfloat16> {};
 
+// Both collisions of one node in the code units of a 16-bit format (the
+// same update as collide, Eqs. 2, 3, 8, 9, 11 and 15-17, 20, divided through
+// by the weights): h[1..8] hold the codes h_i = f_i / w_i - 1/2 and k[0..8]
+// the codes k_i = GS g_i / w_i, and are overwritten with the post-collision
+// codes.  With V as in collide, (f_i^eq + tau_f F_i) / w_i - 1/2 =
+// phi - 1/2 + 3 c_i . V and (g_i^eq + tau_g G_i) GS / w_i = GS (rho s_i / w_i
+// + 3 nu [3 c_i . F + 3 (rho_l - rho_g)(c_i . u)(c_i . grad phi)] + 3 p) for
+// i > 0, GS (rho s_0 / w_0 + 3 p (w_0 - 1) / w_0) for i = 0.  f_0 is not
+// collided: the store writes it as the remainder.  Returns (phi ux, phi uy).
+template <class P>
+__device__ __forceinline__ float2 collide_code(const Model& m, float h[9], float k[9], float phi,
+                                               const Stencil& st, const Macro& M, float2 phiu_prev) {
+    constexpr float GS = P::GS;
+    const float ux = M.ux, uy = M.uy;
+    const float nu = viscosity(m, phi, M.inv_rho);                     // Eqs. 23-26
+    const float omega_g = rcp_approx(fma_rn(3.f, nu, 0.5f));
+    float cu[9];
+    cdot9(ux, uy, cu);
+    const float2 phiu = make_float2(mul(phi, ux), mul(phi, uy));
+    const float Dx = sub(phiu.x, phiu_prev.x);                          // d_t(phi u), Eq. 11
+    const float Dy = sub(phiu.y, phiu_prev.y);
+    const float lam = mul(mul(m.four_over_W, phi), sub(1.f, phi));      // Eq. 3
+    const float phm = sub(phi, 0.5f);
+    float nx_ = 0.f, ny_ = 0.f;
+    if (!m.local_normal) {  // Eq. 2 with the gradient of Eq. 27
+        const float g2 = fma_rn(st.gx, st.gx, mul(st.gy, st.gy));
+        if (g2 > 1e-12f) {
+            const float inv = rsqrt_approx(g2);
+            nx_ = mul(st.gx, inv);
+            ny_ = mul(st.gy, inv);
+        }
+    } else {  // Eq. 29: C = sum c_i (f_i - f_i^eq) + d_t(phi u)/2, n = -C/|C|
+        float ne[9];  // (f_i - f_i^eq) / w_i
+#pragma unroll
+        for (int i = 1; i < 9; ++i) ne[i] = sub(h[i], fma_rn(3.f, cu[i], phm));
+        const float Cx = add(mul(0.5f, Dx), fma_rn(w_of(1), sub(ne[1], ne[3]),
+                                                   mul(w_of(5), add(sub(ne[5], ne[6]), sub(ne[8], ne[7])))));
+        const float Cy = add(mul(0.5f, Dy), fma_rn(w_of(1), sub(ne[2], ne[4]),
+                                                   mul(w_of(5), add(sub(ne[5], ne[8]), sub(ne[6], ne[7])))));
+        const float c2 = fma_rn(Cx, Cx, mul(Cy, Cy));
+        if (c2 > 1e-12f) {
+            const float inv = rsqrt_approx(c2);
+            nx_ = -mul(Cx, inv);
+            ny_ = -mul(Cy, inv);
+        }
+    }
+    // Allen-Cahn, Eqs. 8, 9, 11 (first, so c_i . V is dead before the g terms)
+    {
+        const float l3 = mul(lam, 1.f / 3.f);
+        float cv[9];
+        cdot9(fma_rn(m.tau_f_mh, fma_rn(l3, nx_, Dx), phiu.x),
+              fma_rn(m.tau_f_mh, fma_rn(l3, ny_, Dy), phiu.y), cv);   // c_i . V
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const float he = fma_rn(3.f, cv[i], phm);
+            h[i] = fma_rn(m.inv_tau_f, sub(he, h[i]), h[i]);
+        }
+    }
+    // Navier-Stokes, Eqs. 15-17, 20
+    float ch[9], ce[9];
+    const float nu9 = mul(9.f * GS, nu);                          // GS scalings are exact
+    cdot9(mul(nu9, M.Fx), mul(nu9, M.Fy), ch);                    // GS c_i . 3 nu 3F
+    const float e9 = mul(nu9, m.drho);
+    cdot9(mul(e9, st.gx), mul(e9, st.gy), ce);                    // GS c_i . 3 nu 3 (rho_l - rho_g) grad phi
+    const float p3 = mul(3.f * GS, M.p);
+    const float rho = mul(GS, M.rho);
+    const float m15 = mul(-1.5f, M.usq);
+    {
+        const float ke0 = fma_rn(rho, m15, mul(p3, (w_of(0) - 1.f) / w_of(0)));
+        k[0] = fma_rn(omega_g, sub(ke0, k[0]), k[0]);
+    }
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const float s = fma_rn(cu[i], fma_rn(4.5f, cu[i], 3.f), m15);   // s_i / w_i
+        const float t = add(fma_rn(cu[i], ce[i], ch[i]), p3);
+        const float ke = fma_rn(rho, s, t);
+        k[i] = fma_rn(omega_g, sub(ke, k[i]), k[i]);
+    }
+    return phiu;
+}
+
+// The collision of the storage format ST: on populations (FP32) or on codes.
+template <int ST>
+__device__ __forceinline__ float2 collide_st(const Model& m, float f[9], float g[9], float phi,
+                                             const Stencil& st, const Macro& M, float2 prev) {
+    if constexpr (ST == ST_FP32)
+        return collide(m, f, g, phi, st, M, prev);
+    else
+        return collide_code<Pop<ST>>(m, f, g, phi, st, M, prev);
+}
+
 // Pull (stream) node q through a 16-bit storage format: the nine loads first
 // (f_0 and g_0, and one word of (f_i, g_i) codes per moving direction), then
-// the decodes.  The six wall-dependent loads sit in a branch that is uniform
-// across a warp (BR; a warp covers part of one tile row), or are per-lane
-// selects.  G: decode g as well.
+// the conversions of the codes to FP32 (f[0] is the FP32 value of f_0,
+// f[1..8] and g[0..8] are the codes h_i and k_i).  The six wall-dependent
+// loads sit in a branch that is uniform across a warp (BR; a warp covers part
+// of one tile row), or are per-lane selects.  G: convert g as well.
 template <int ST, bool BR, bool G>
 __device__ __forceinline__ void pull_16(const void* fs, const void* gs, int N, const Nbr& q,
                                         float f[9], float g[9]) {
@@ -227,15 +371,16 @@ __device__ __forceinline__ void pull_16(const void* fs, const void* gs, int N, c
         w[7] = raw(7, q.rp + q.xp);
         w[8] = raw(8, q.rp + q.xm);
     }
-    // a bounce-back link decodes with the stored direction's weight: opposite
-    // directions share w_i, so the stored and the pulled index agree on it
+    // the codes as floats; a bounce-back link takes the code of the stored
+    // direction, which has the pulled direction's weight (opposite directions
+    // share w_i), so the code means the same population in either
     f[0] = f0;
 #pragma unroll
-    for (int i = 1; i < 9; ++i) f[i] = P::dec_f(i, P::lo(w[i]));
+    for (int i = 1; i < 9; ++i) f[i] = P::C::to_f(P::lo(w[i]));
     if (G) {
-        g[0] = P::dec_g(0, g0);
+        g[0] = P::C::to_f(g0);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) g[i] = P::dec_g(i, P::hi(w[i]));
+        for (int i = 1; i < 9; ++i) g[i] = P::C::to_f(P::hi(w[i]));
     }
 }
 
@@ -267,7 +412,7 @@ __device__ __forceinline__ float phi_at_st(const void* fs, int N, int x, int y, 
                                            int walls) {
     float v[9];
     pull9f<ST, WALLS>(fs, N, make_nbr<WALLS>(x, y, nx, ny, walls), v);
-    return sum9(v);
+    return Pop<ST>::phi_of(v);
 }
 
 }  // namespace lbmpf

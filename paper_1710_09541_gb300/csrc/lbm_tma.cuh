@@ -258,4 +258,213 @@ __global__ void __launch_bounds__(NT, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// The step with 16-bit storage (Shifted16) and TMA-staged tiles: one TX x TY
+// tile per CTA, many CTAs per SM.  Thread 0 copies the tile's pulls and its
+// one-node phi ring into shared memory with two bulk tensor copies:
+//   word box [8][TY+4][TX+8]  the (f_i, g_i) code words of the 8 moving
+//             directions, rows y0-2 .. y0+TY+1, columns x0-4 .. x0+TX+3
+//   f_0 box  [TY+2][TX+8]     rows y0-1 .. y0+TY, same columns
+// (x starts 4 columns early so it is 16-byte aligned).  Every pull is then a
+// shared-memory load at a fixed offset from the node's slot, so the pulls of
+// the tile and of the ring need no address arithmetic and no wrap logic: the
+// copies fill coordinates outside the grid with zeros, and tiles on a
+// periodic edge patch those entries with the wrapped values from global
+// memory before the pulls.  The arithmetic is the shared tile body's (same
+// functions, same order), so the results equal the direct-load kernel's bit
+// for bit.  The mbarrier wait is bounded; a timeout sets bit 1 of the status
+// flag, the CTA waits (bounded) once more for its copies and returns.
+// ---------------------------------------------------------------------------
+template <int TX, int TY>
+struct Tma16Tile {
+    static constexpr int BW = TX + 8;   // box row length (words)
+    static constexpr int WH = TY + 4;   // word box rows
+    static constexpr int FH = TY + 2;   // f_0 box rows
+    static constexpr int WP = WH * BW;  // one direction's plane in the word box
+    static constexpr uint32_t W_BYTES = 8u * WP * 4u;
+    static constexpr uint32_t F_BYTES = uint32_t(FH) * BW * 4u;
+    static constexpr uint32_t COPY_BYTES = W_BYTES + F_BYTES;
+    static_assert(BW % 4 == 0 && (W_BYTES % 128) == 0, "16-byte rows, 128-byte aligned f_0 box");
+    static_assert(COPY_BYTES < (1u << 20), "mbarrier transaction count");
+};
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Pull of one node's 8 moving code words from the word box; o = the node's
+// slot (row * BW + column).  lo / hi: the node sits on the wall at y = -1/2 /
+// y = ny - 1/2 (half-way bounce-back: the link returns the node's own word of
+// the opposite direction); top_open: the node is the top row under the open
+// top (its c_y = -1 links pull from its own row).
+template <int BW, int WP>
+__device__ __forceinline__ void pull_words_smem(const unsigned int* B, int o, bool lo, bool hi,
+                                                bool top_open, unsigned int w[9]) {
+    // plane k - 1 holds direction k
+    w[1] = B[0 * WP + o - 1];
+    w[3] = B[2 * WP + o + 1];
+    if (lo || hi || top_open) {
+        const int up = top_open ? 0 : BW;  // row the c_y = -1 links pull from
+        w[2] = lo ? B[3 * WP + o] : B[1 * WP + o - BW];
+        w[4] = hi ? B[1 * WP + o] : B[3 * WP + o + up];
+        w[5] = lo ? B[6 * WP + o] : B[4 * WP + o - BW - 1];
+        w[6] = lo ? B[7 * WP + o] : B[5 * WP + o - BW + 1];
+        w[7] = hi ? B[4 * WP + o] : B[6 * WP + o + up + 1];
+        w[8] = hi ? B[5 * WP + o] : B[7 * WP + o + up - 1];
+    } else {
+        w[2] = B[1 * WP + o - BW];
+        w[4] = B[3 * WP + o + BW];
+        w[5] = B[4 * WP + o - BW - 1];
+        w[6] = B[5 * WP + o - BW + 1];
+        w[7] = B[6 * WP + o + BW + 1];
+        w[8] = B[7 * WP + o + BW - 1];
+    }
+}
+
+// WALLS: 0 periodic in y, 1 a wall at y = 0 and the kind of top read from
+// m.walls (closed: 1, open: 2).  The same residency as the direct-load
+// 16-bit kernels.
+template <int TX, int TY, int ST, int WALLS>
+__global__ void __launch_bounds__(TX* TY, (WALLS == 0 ? 9 : 10))
+    k_step16_tma(const __grid_constant__ CUtensorMap tm_w, const __grid_constant__ CUtensorMap tm_f0,
+                 const void* __restrict__ fs, const void* __restrict__ gs, void* __restrict__ fd,
+                 void* __restrict__ gd, float* __restrict__ phiu, unsigned int* __restrict__ flag,
+                 int nx, int ny, Model m) {
+    using P = Pop<ST>;
+    using T = Tma16Tile<TX, TY>;
+    constexpr int BW = T::BW, WH = T::WH, WP = T::WP;
+    __shared__ __align__(128) unsigned int sw[8 * WP];
+    __shared__ __align__(128) float sf0[T::FH * BW];
+    __shared__ float sphi[TY + 2][TX + 2];
+    __shared__ __align__(8) uint64_t bar;
+    if (WALLS == 0) m.walls = 0;
+    const int walls = m.walls;
+    const bool open_top = walls == 2;
+    const int N = nx * ny;  // 20 N < 2^31 (checked at create)
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = (x < nx) && (y < ny);
+
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    griddep_wait();
+    griddep_launch();
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&bar, T::COPY_BYTES);
+        tma_load_3d(sw, &tm_w, &bar, x0 - 4, y0 - 2, 0);
+        tma_load_2d(sf0, &tm_f0, &bar, x0 - 4, y0 - 1);
+    }
+    // the node's own loads go out while the copies are in flight
+    float2 prev = make_float2(0.f, 0.f);
+    unsigned short g0 = 0;
+    if (active) {
+        prev = make_float2(phiu[y * nx + x], phiu[N + y * nx + x]);
+        g0 = __ldg(static_cast<const unsigned short*>(gs) + (y * nx + x));
+    }
+    const bool got = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!got)) {
+        if (tid == 0) {
+            atomicOr(flag, 2u);
+            mbar_wait_bounded(&bar, 0);  // the late copies may still land
+        }
+        return;
+    }
+
+    // periodic edges: the entries the pulls read outside the grid take the
+    // wrapped values (walls: rows outside the grid are never read)
+    const bool edge_x = (x0 - 2 < 0) || (x0 + TX + 2 > nx);
+    const bool edge_y = walls == 0 && ((y0 - 2 < 0) || (y0 + TY + 2 > ny));
+    if (edge_x || edge_y) {
+        const unsigned int* W = P::pw(fs, N);
+        constexpr int CW = TX + 4;  // box columns 2 .. TX+5 are read
+        for (int e = tid; e < 8 * WH * CW; e += TX * TY) {
+            const int k = e / (WH * CW), rem = e - k * (WH * CW);
+            const int r = rem / CW, c = 2 + rem % CW;
+            const int gx = x0 - 4 + c, gy = y0 - 2 + r;
+            const bool ox = gx < 0 || gx >= nx, oy = gy < 0 || gy >= ny;
+            if ((ox || oy) && (walls == 0 || !oy))
+                sw[k * WP + r * BW + c] = __ldg(W + (k * N + fold_y(gy, ny, 0) * nx + fold_x(gx, nx)));
+        }
+        const float* F0 = static_cast<const float*>(fs);
+        constexpr int CF = TX + 2;  // f_0 box columns 3 .. TX+4 are read
+        for (int e = tid; e < T::FH * CF; e += TX * TY) {
+            const int r = e / CF, c = 3 + e % CF;
+            const int gx = x0 - 4 + c, gy = y0 - 1 + r;
+            const bool ox = gx < 0 || gx >= nx, oy = gy < 0 || gy >= ny;
+            if ((ox || oy) && (walls == 0 || !oy))
+                sf0[r * BW + c] = __ldg(F0 + (fold_y(gy, ny, 0) * nx + fold_x(gx, nx)));
+        }
+        __syncthreads();
+    }
+
+    // phi (Eq. 12) of a tile or ring slot (lx, ly), -1 <= lx <= TX,
+    // -1 <= ly <= TY: at a wall the ghost row is the edge row (mirror), and
+    // a slot below or above the grid takes the edge row's phi
+    auto phi_slot = [&](int lx, int ly, unsigned int w[9], float& f0) {
+        int gy = y0 + ly;
+        if (walls && (gy < 0 || gy >= ny)) gy = gy < 0 ? 0 : ny - 1;
+        int br = gy - y0 + 2;  // word box row
+#if LBM_DEBUG_CHECKS
+        // the slot and its pulls stay inside the boxes: rows br - 1 .. br + 1
+        // of the word box, columns lx + 3 .. lx + 5
+        if (br < 1 || br > TY + 2 || lx < -1 || lx > TX) {
+            atomicOr(flag, 4u);
+            br = 2;
+            lx = 0;
+        }
+#endif
+        const bool lo = walls && gy == 0, hi = walls && !open_top && gy == ny - 1;
+        const bool top = open_top && gy == ny - 1;
+        pull_words_smem<BW, WP>(sw, br * BW + lx + 4, lo, hi, top, w);
+        f0 = sf0[(br - 1) * BW + lx + 4];
+        float h[9];
+        h[0] = f0;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) h[i] = P::C::to_f(P::lo(w[i]));
+        return P::phi_of(h);
+    };
+    unsigned int w[9];
+    float f0;
+    sphi[ty + 1][tx + 1] = phi_slot(tx, ty, w, f0);
+    for (int r = tid; r < Ring<TX, TY>::count; r += TX * TY) {
+        int lx, ly;
+        Ring<TX, TY>::pos(r, lx, ly);
+        unsigned int wr[9];
+        float f0r;
+        sphi[ly + 1][lx + 1] = phi_slot(lx, ly, wr, f0r);
+    }
+    __syncthreads();
+    if (!active) return;
+
+    float h[9], k[9];
+    h[0] = f0;
+    k[0] = P::C::to_f(g0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        h[i] = P::C::to_f(P::lo(w[i]));
+        k[i] = P::C::to_f(P::hi(w[i]));
+    }
+    const int lx = tx + 1, ly = ty + 1;
+    const float phi = sphi[ly][lx];
+    const Stencil st = stencil(phi, sphi[ly][lx + 1], sphi[ly][lx - 1], sphi[ly + 1][lx],
+                               sphi[ly - 1][lx], sphi[ly + 1][lx + 1], sphi[ly + 1][lx - 1],
+                               sphi[ly - 1][lx - 1], sphi[ly - 1][lx + 1]);
+    const Macro M = macro_from(m, P::gmom(k), phi, st.gx, st.gy, st.lap);
+    if (!isfinite(add(add(phi, M.ux), add(M.uy, M.p)))) report_nonfinite(flag);
+    const float2 now = collide_code<P>(m, h, k, phi, st, M, prev);
+    const int n = y * nx + x;
+    phiu[n] = now.x;
+    phiu[N + n] = now.y;
+    P::stfg(fd, gd, N, n, h, k, phi);
+}
+
 }  // namespace lbmpf

@@ -265,16 +265,33 @@ def test_layered_poiseuille_table1_ratio10():
     assert u[:ny // 2].max() < u[ny // 2:].max()   # the gas layer (upper) moves faster
 
 
-def _layered_Eu(ratio, nu_ratio, ny, W, steps):
+def _layered_Eu(ratio, nu_ratio, ny, W, steps, visc_mode=2):
     """E_u (Eq. 32) of the layered Poiseuille flow of Sec. III B on a 4 x ny
     channel, started from Eq. 31 itself."""
     rho_l, nu_l, uc, h = 1.0, 0.1, 1e-4, ny / 2
-    P = dict(rho_l=rho_l, rho_g=rho_l / ratio, nu_l=nu_l, nu_g=nu_ratio * nu_l, visc_mode=2, sigma=1e-3,
-             W=W, tau_h=0.8, bc_y=1)
+    P = dict(rho_l=rho_l, rho_g=rho_l / ratio, nu_l=nu_l, nu_g=nu_ratio * nu_l, visc_mode=visc_mode,
+             sigma=1e-3, W=W, tau_h=0.8, bc_y=1)
     P["Gx"] = uc * (rho_l * nu_l + P["rho_g"] * P["nu_g"]) / h ** 2
     ua = _two_layer_profile(ny, P)
     u = _poiseuille(ny, 4, P, steps, ua)
     return np.abs(u - ua).sum() / np.abs(ua).sum()
+
+
+def test_layered_poiseuille_linear_viscosity_matches_table1_comparison_column():
+    """Table 1's setup with the viscosity interpolated linearly (Eq. 24; with
+    nu_g = nu_l this is a uniform nu, so mu follows rho): E_u reproduces the
+    paper's column for the model of Fakhari et al. within 5% at density
+    ratios 100 and 1000 (measured 2.71e-1 and 3.84e-1 against 2.7e-1 and
+    3.9e-1).  At this setup E_u is set by the smooth viscosity across the
+    interface rather than by the LB scheme, so the printed numbers pin the
+    setup the two models share: the grid, W, the node placement and the
+    interface position against the half-way walls (the placement as printed,
+    phi0 and Eq. 31 at y = j, gives 2.93e-1 at ratio 100, 8.5% off).  E_u
+    does not depend on G_x: the steady profile and Eq. 31 both scale with it."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "table1_poiseuille_Eu_comparison.txt"))
+    for ratio, nu_ratio, Eu_paper in rows[[1, 3]]:
+        Eu = _layered_Eu(ratio, nu_ratio, 100, 5.0, 60000, visc_mode=0)
+        assert abs(Eu / Eu_paper - 1) < 0.05, (ratio, Eu, Eu_paper)
 
 
 @pytest.mark.parametrize("ratio,nu_ratio", [(100.0, 1.0), (1000.0, 10.0)])
