@@ -80,16 +80,12 @@ enum {
                                    2^10 g_i/w_i (38 B/node) */
     LBM_STORE_BF16_SHIFTED = 2  /* as FP16_SHIFTED with BF16 and g unscaled */
 };
-/* step kernel (kernel); all compute the same arithmetic and give the same bits */
+/* step kernel (kernel) */
 enum {
-    LBM_KERNEL_AUTO = 0,    /* the faster on GB300: LBM_KERNEL_GENERIC with FP32 storage;
-                               LBM_KERNEL_TMA with 16-bit storage where the grid allows it,
-                               else LBM_KERNEL_GENERIC */
-    LBM_KERNEL_GENERIC = 1, /* 32 x 4 tiles, one thread per node, direct loads; any grid */
-    LBM_KERNEL_TMA = 2      /* tiles staged in shared memory by bulk tensor copies.  FP32
-                               storage: a persistent kernel (nx % 4 == 0, nx >= 72, ny >= 20,
-                               no open top); 16-bit storage: one 32 x 4 tile per CTA
-                               (nx % 4 == 0, nx >= 40, ny >= 8) */
+    LBM_KERNEL_AUTO = 0,    /* the library's choice: currently LBM_KERNEL_GENERIC */
+    LBM_KERNEL_GENERIC = 1  /* tiles of 32 x 4 threads, direct loads, phi ring recomputed
+                               in shared memory; one node per thread with FP32 storage,
+                               two with 16-bit storage; any grid */
 };
 
 typedef struct {
@@ -323,19 +319,6 @@ lbm_status lbm_laplace_jump(lbm_handle* h, double xc, double yc, double r_in, do
                             double* dp);
 lbm_status lbm_probe(lbm_handle* h, int npts, const int* x, const int* y, double* phi, double* rho,
                      double* ux, double* uy, double* p);
-
-/*
- * lbm_selftest_bounded_wait -- exercise the timeout path of the bounded
- *   mbarrier waits of the TMA-staged step kernel: a one-block kernel arms an
- *   mbarrier for bytes that no copy will deliver (none is issued), waits with
- *   the kernel's own bounded-wait routine and a short limit, and records the
- *   timeout the way the staged kernel does.  *timed_out = 1 when the wait gave
- *   up (the expected result), after which the device stays usable.  The paper
- *   has no counterpart; this checks this library's failure handling.
- *   stream: cudaStream_t or NULL.  Errors: LBM_ERR_INVALID (NULL output),
- *   LBM_ERR_CUDA.
- */
-lbm_status lbm_selftest_bounded_wait(void* stream, int* timed_out);
 
 /* lbm_synchronize -- wait for all work enqueued by this handle. */
 lbm_status lbm_synchronize(lbm_handle* h);

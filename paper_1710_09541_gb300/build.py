@@ -15,8 +15,7 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 SRC = os.path.join(PKG, "csrc", "lbm_pf.cu")
-DEPS = [SRC, os.path.join(PKG, "csrc", "lbm_kernels.cuh"), os.path.join(PKG, "csrc", "lbm_tma.cuh"),
-        os.path.join(PKG, "csrc", "lbm_store.cuh"),
+DEPS = [SRC, os.path.join(PKG, "csrc", "lbm_kernels.cuh"), os.path.join(PKG, "csrc", "lbm_store.cuh"),
         os.path.join(ROOT, "include", "lbm_pf.h")]
 LIB_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIB_DIR, "liblbm_pf.so")

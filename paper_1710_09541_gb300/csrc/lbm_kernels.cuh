@@ -113,9 +113,9 @@ __device__ __forceinline__ void pull9(const float* __restrict__ s, size_t Nz, co
 
 // Explicitly rounded FP32 operations.  All arithmetic of the step goes
 // through these, so no multiply-add contraction is left to the compiler and
-// every kernel that inlines the functions below (direct-load, TMA-staged,
-// field read-back, initialisation) produces the same bits for the same
-// inputs.  Additions, multiplications and fused multiply-adds are IEEE
+// every kernel that inlines the functions below (single-case and batched
+// steps, field read-back, initialisation, probes) produces the same bits for
+// the same inputs.  Additions, multiplications and fused multiply-adds are IEEE
 // round-to-nearest.  The step has no division or square root: the five
 // reciprocals it needs, 1/rho (Eq. 22a), 1/tau_g (Eq. 23), 1/(interpolated
 // 1/nu) (Eq. 25), 1/|grad phi| (Eq. 2) and 1/|C| (Eq. 29), use the hardware

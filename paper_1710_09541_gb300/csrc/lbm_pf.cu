@@ -18,7 +18,6 @@
 #include "lbm_kernels.cuh"
 #include "lbm_pf.h"
 #include "lbm_store.cuh"
-#include "lbm_tma.cuh"
 
 using namespace lbmpf;
 
@@ -76,24 +75,24 @@ __device__ __forceinline__ bool nbr_in_range(const Nbr& q, int nx, int ny) {
 #ifndef LBM_PREFETCH_PER10SM
 #define LBM_PREFETCH_PER10SM 20
 #endif
+// prefetch distance of the 16-bit step kernels, in tiles per 10 SMs
+#ifndef LBM_PREFETCH16_PER10SM
+#define LBM_PREFETCH16_PER10SM 20
+#endif
 // prefetch with 16-bit storage too (off: those steps are instruction-bound,
 // and the requests cost more than they hide: FP16 at 2048^2 47.6 k -> 45.5 k
 // MLUPS, BF16 47.5 k -> 44.5 k, at their tuned residency)
 #ifndef LBM_PREFETCH_16
-#define LBM_PREFETCH_16 0
+#define LBM_PREFETCH_16 1
 #endif
 // also prefetch the tile two distances ahead
 #ifndef LBM_PREFETCH_TWICE
 #define LBM_PREFETCH_TWICE 0
 #endif
-// grids with fewer tiles than this many prefetch distances step without it
-// LBM_KERNEL_AUTO with 16-bit storage takes the TMA-staged kernel where the
-// grid allows it (nx % 4 == 0)
-#ifndef LBM_AUTO_TMA16
-#define LBM_AUTO_TMA16 0
-#endif
-#ifndef LBM_PREFETCH_MIN_TILES_X
-#define LBM_PREFETCH_MIN_TILES_X 16
+// steps whose algorithmic traffic is below this many tenths of the L2 size
+// run without the prefetch
+#ifndef LBM_PREFETCH_L2X10
+#define LBM_PREFETCH_L2X10 15
 #endif
 // One TX x TY tile with origin (x0, y0): the body shared by the single-case
 // step kernel and the batched kernel (so both give the same bits).
@@ -187,21 +186,114 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
     Pop<ST>::stfg(fd, gd, N32, n32, f, g, phi);
 }
 
+// One TX x (NPT TY) tile with 16-bit storage: each of the TX x TY threads
+// takes NPT nodes, in rows ty, ty + TY, ...  Between the two phases a node
+// holds its nine raw code words rather than 18 converted values, so that two
+// nodes per thread fit the register budget; the codes are converted where they
+// are used.  The arithmetic is step_tile's (same functions, same order), so a
+// node gets the same bits whichever body, tile shape or kernel steps it.
+#ifndef LBM_NPT16
+#define LBM_NPT16 2
+#endif
+template <int TX, int TY, int NPT, int WALLS, int ST>
+__device__ __forceinline__ void step_tile16(float (*sphi)[TX + 2], const void* __restrict__ fs,
+                                            const void* __restrict__ gs, void* __restrict__ fd,
+                                            void* __restrict__ gd, float* __restrict__ phiu,
+                                            unsigned int* __restrict__ flag, int nx, int ny, Model m,
+                                            int x0, int y0) {
+    constexpr bool BR = (WALLS < 0) || LBM_WALL_BRANCH;
+    constexpr int TH = TY * NPT;
+    if (WALLS == 0) m.walls = 0;  // WALLS == 1 keeps the kind of top (wall or open)
+    const int wfold = WALLS >= 0 ? WALLS : m.walls;  // y folding: wrap (0) or clamp
+    const int N = nx * ny;  // 20 N < 2^31 (checked at create): 32-bit offsets
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = x0 + tx;
+    unsigned int w[NPT][9];
+    float f0[NPT];
+    unsigned short g0[NPT];
+    float2 prev[NPT];
+    int n[NPT];
+    bool act[NPT];
+#if LBM_DEBUG_CHECKS
+    for (int k = ty * TX + tx; k < (TH + 2) * (TX + 2); k += TX * TY)
+        (&sphi[0][0])[k] = __int_as_float(0x7fc00000);
+    __syncthreads();
+#endif
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int ly = ty + TY * j, y = y0 + ly;
+        act[j] = (x < nx) && (y < ny);
+        n[j] = 0;
+        prev[j] = make_float2(0.f, 0.f);
+        if (act[j]) {
+            Nbr q = make_nbr<WALLS>(x, y, nx, ny, m.walls);
+#if LBM_DEBUG_CHECKS
+            if (!nbr_in_range(q, nx, ny)) {  // record, and pull node 0 instead
+                atomicOr(flag, 4u);
+                q = make_nbr<WALLS>(0, 0, nx, ny, m.walls);
+            }
+#endif
+            n[j] = q.r0 + q.x;
+            prev[j] = make_float2(phiu[n[j]], phiu[N + n[j]]);
+            pull_words16<ST, BR, true>(fs, gs, N, q, w[j], f0[j], g0[j]);
+            float h[9];
+            codes_f<ST>(w[j], f0[j], h);
+            sphi[ly + 1][tx + 1] = Pop<ST>::phi_of(h);
+        } else {
+            sphi[ly + 1][tx + 1] =
+                phi_at_st<ST, WALLS>(fs, N, fold_x(x, nx), fold_y(y, ny, wfold), nx, ny, m.walls);
+        }
+    }
+    for (int r = ty * TX + tx; r < Ring<TX, TH>::count; r += TX * TY) {
+        int lx, ly;
+        Ring<TX, TH>::pos(r, lx, ly);
+#if LBM_DEBUG_CHECKS
+        const int fx = fold_x(x0 + lx, nx), fy = fold_y(y0 + ly, ny, wfold);
+        if (lx < -1 || lx > TX || ly < -1 || ly > TH || fx < 0 || fx >= nx || fy < 0 || fy >= ny) {
+            atomicOr(flag, 4u);
+            continue;
+        }
+#endif
+        sphi[ly + 1][lx + 1] = phi_at_st<ST, WALLS>(fs, N, fold_x(x0 + lx, nx),
+                                                    fold_y(y0 + ly, ny, wfold), nx, ny, m.walls);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        if (!act[j]) continue;
+        const int lx = tx + 1, ly = ty + TY * j + 1;
+        float h[9], k[9];
+        codes_f<ST>(w[j], f0[j], h);
+        codes_g<ST>(w[j], g0[j], k);
+        const float phi = sphi[ly][lx];
+        const Stencil st = stencil(phi, sphi[ly][lx + 1], sphi[ly][lx - 1], sphi[ly + 1][lx],
+                                   sphi[ly - 1][lx], sphi[ly + 1][lx + 1], sphi[ly + 1][lx - 1],
+                                   sphi[ly - 1][lx - 1], sphi[ly - 1][lx + 1]);
+        const Macro M = macro_from(m, Pop<ST>::gmom(k), phi, st.gx, st.gy, st.lap);
+        if (!isfinite(add(add(phi, M.ux), add(M.uy, M.p)))) report_nonfinite(flag);
+        const float2 now = collide_code<Pop<ST>>(m, h, k, phi, st, M, prev[j]);
+        phiu[n[j]] = now.x;
+        phiu[N + n[j]] = now.y;
+        Pop<ST>::stfg(fd, gd, N, n[j], h, k, phi);
+    }
+}
+
 __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// Ask L2 for the rows tile (bx, by) will pull: rows by*TY - 1 .. by*TY + TY
-// of the 18 population planes and the TY rows of (phi u), from column bx*TX
-// (one request per row and plane).  Called by a block for the tile that
-// starts about a third of a resident wave after it, so those DRAM reads are in
-// flight while the current tiles compute: the step is bound by load latency,
-// and a prefetch holds no register and no shared memory.
-template <int TX, int TY, int ST>
+// Ask L2 for the rows tile (bx, by) of TX x TY nodes will pull: rows
+// by*TY - 1 .. by*TY + TY of the population planes and the TY rows of (phi u),
+// from column bx*TX (one request per row and plane, one per thread of the NT
+// threads).  Called by a block for the tile that starts about a fifth of a
+// resident wave after it, so those DRAM reads are in flight while the current
+// tiles compute: the step is bound by load latency, and a prefetch holds no
+// register and no shared memory.
+template <int TX, int TY, int NT, int ST>
 __device__ __forceinline__ void prefetch_tile(const void* fs, const void* gs, const float* phiu,
                                               int nx, int ny, int wfold, int bx, int by) {
     constexpr int NP = Pop<ST>::PLANES;
-    static_assert(NP * (TY + 2) + 2 * TY <= TX * TY, "one request per thread");
+    static_assert(NP * (TY + 2) + 2 * TY <= NT, "one request per thread");
     const int N = nx * ny;
     const int t = threadIdx.y * TX + threadIdx.x;
     const int x0 = bx * TX;
@@ -228,7 +320,14 @@ constexpr int step_minb() {
     if (LBM_STEP_MINB > 0) return LBM_STEP_MINB;
     if (FIELDS) return 8;
     if (ST == ST_FP32) return WALLS == 0 ? 10 : 9;
+    if (LBM_NPT16 > 1) return 8;  // two nodes per thread: 64 registers, no spills
     return WALLS == 0 ? 9 : 10;
+}
+
+// nodes per thread of a step kernel: LBM_NPT16 for 16-bit steps, else 1
+template <bool FIELDS, int ST>
+__host__ __device__ constexpr int step_npt() {
+    return (!FIELDS && ST != ST_FP32) ? LBM_NPT16 : 1;
 }
 
 template <int TX, int TY, bool FIELDS, int WALLS, int ST>
@@ -236,25 +335,32 @@ __global__ void __launch_bounds__(TX* TY, (step_minb<FIELDS, WALLS, ST>()))
     k_step(const float* __restrict__ fs, const float* __restrict__ gs, float* __restrict__ fd,
            float* __restrict__ gd, float* __restrict__ phiu, unsigned int* __restrict__ flag,
            double* __restrict__ out, int nx, int ny, Model m, int pf_ahead) {
-    __shared__ float sphi[TY + 2][TX + 2];
+    constexpr int NPT = step_npt<FIELDS, ST>();
+    __shared__ float sphi[TY * NPT + 2][TX + 2];
     griddep_wait();
     griddep_launch();
     if constexpr (!FIELDS && (ST == ST_FP32 || LBM_PREFETCH_16)) {
         if (pf_ahead > 0) {
             const int lin = blockIdx.y * gridDim.x + blockIdx.x + pf_ahead;
             if (lin < gridDim.x * gridDim.y)
-                prefetch_tile<TX, TY, ST>(fs, gs, phiu, nx, ny, WALLS >= 0 ? WALLS : m.walls,
-                                          lin % gridDim.x, lin / gridDim.x);
+                prefetch_tile<TX, TY * NPT, TX * TY, ST>(fs, gs, phiu, nx, ny,
+                                                         WALLS >= 0 ? WALLS : m.walls,
+                                                         lin % gridDim.x, lin / gridDim.x);
 #if LBM_PREFETCH_TWICE
             const int lin2 = lin + pf_ahead;
             if (lin2 < gridDim.x * gridDim.y)
-                prefetch_tile<TX, TY, ST>(fs, gs, phiu, nx, ny, WALLS >= 0 ? WALLS : m.walls,
-                                          lin2 % gridDim.x, lin2 / gridDim.x);
+                prefetch_tile<TX, TY * NPT, TX * TY, ST>(fs, gs, phiu, nx, ny,
+                                                         WALLS >= 0 ? WALLS : m.walls,
+                                                         lin2 % gridDim.x, lin2 / gridDim.x);
 #endif
         }
     }
-    step_tile<TX, TY, FIELDS, WALLS, ST>(sphi, fs, gs, fd, gd, phiu, flag, out, nx, ny, m,
-                                         blockIdx.x * TX, blockIdx.y * TY);
+    if constexpr (NPT > 1 || (!FIELDS && ST != ST_FP32))
+        step_tile16<TX, TY, NPT, WALLS, ST>(sphi, fs, gs, fd, gd, phiu, flag, nx, ny, m,
+                                            blockIdx.x * TX, blockIdx.y * TY * NPT);
+    else
+        step_tile<TX, TY, FIELDS, WALLS, ST>(sphi, fs, gs, fd, gd, phiu, flag, out, nx, ny, m,
+                                             blockIdx.x * TX, blockIdx.y * TY);
 }
 
 // ---------------------------------------------------------------------------
@@ -460,12 +566,6 @@ __global__ void __launch_bounds__(RED_THREADS)
 constexpr int STEP_TX = LBM_STEP_TX;
 constexpr int STEP_TY = LBM_STEP_TY;
 constexpr int RED_BLOCKS = 1216;  // 8 x 152 SMs
-// TMA-staged step: 64 x 16 tiles, one node per thread, two stages (213 KB)
-constexpr int TMA_TX = 64;
-constexpr int TMA_TY = 16;
-constexpr int TMA_NT = TMA_TX * TMA_TY;
-using TmaCfg = TmaTile<TMA_TX, TMA_TY>;
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -488,15 +588,8 @@ struct lbm_handle {
     unsigned int* flag = nullptr;
     bool inited = false;
     long long since_check = 0;
-    // TMA-staged step kernels: the persistent FP32 one (LBM_KERNEL_TMA with
-    // FP32 storage) and the one-tile-per-CTA 16-bit one (use_tma16)
-    bool use_tma = false;
-    bool use_tma16 = false;
-    CUtensorMap tm_w[2], tm_f0[2];  // 16-bit: word planes and f_0 plane of each buffer
     int pf_ahead = 0;  // L2 prefetch distance of the step kernel, in tiles
     bool owns_memory = true;  // false: the device buffers live in a caller's workspace
-    CUtensorMap tm_f[2], tm_g[2], tm_u;
-    int tiles_x = 0, ntiles = 0, tma_grid = 0;
     char err[512] = {0};
 };
 
@@ -543,18 +636,8 @@ static lbm_status validate(int nx, int ny, const lbm_params* p, char* msg, size_
         p->storage != LBM_STORE_BF16_SHIFTED)
         return bad("storage must be LBM_STORE_FP32, _FP16_SHIFTED or _BF16_SHIFTED");
     if (p->check_every < 0) return bad("check_every must be >= 0");
-    if (p->kernel < LBM_KERNEL_AUTO || p->kernel > LBM_KERNEL_TMA)
-        return bad("kernel must be LBM_KERNEL_AUTO, _GENERIC or _TMA");
-    if (p->kernel == LBM_KERNEL_TMA && p->storage != LBM_STORE_FP32 &&
-        !(nx % 4 == 0 && nx >= 40 && ny >= 8))
-        return bad("LBM_KERNEL_TMA with 16-bit storage needs nx % 4 == 0 (16-byte row pitch), "
-                   "nx >= 40 and ny >= 8 (the staged box fits in the grid)");
-    if (p->kernel == LBM_KERNEL_TMA && p->storage == LBM_STORE_FP32 && p->bc_y == LBM_BC_WALL_OPEN)
-        return bad("LBM_KERNEL_TMA with FP32 storage supports periodic and walled y boundaries only");
-    if (p->kernel == LBM_KERNEL_TMA && p->storage == LBM_STORE_FP32 &&
-        !(nx % 4 == 0 && nx >= 72 && ny >= 20))
-        return bad("LBM_KERNEL_TMA with FP32 storage needs nx % 4 == 0 (16-byte row pitch), "
-                   "nx >= 72 and ny >= 20 (the staged box fits in the grid)");
+    if (p->kernel != LBM_KERNEL_AUTO && p->kernel != LBM_KERNEL_GENERIC)
+        return bad("kernel must be LBM_KERNEL_AUTO or LBM_KERNEL_GENERIC");
     return LBM_OK;
 }
 
@@ -655,29 +738,10 @@ static cudaError_t launch_dep(void (*k)(Exp...), dim3 grid, dim3 block, cudaStre
 static lbm_status launch_step(lbm_handle* h, bool fields, double* out) {
     const int c = h->cur;
     const bool walls = h->model.walls != 0;
-    if (!fields && h->use_tma) {
-        auto k = walls ? k_step_tma<TMA_TX, TMA_TY, TMA_NT, 1> : k_step_tma<TMA_TX, TMA_TY, TMA_NT, 0>;
-        k<<<h->tma_grid, TMA_NT, TmaCfg::SMEM, h->stream>>>(
-            h->tm_f[c], h->tm_g[c], h->tm_u, h->f[c], h->g[c], h->f[c ^ 1], h->g[c ^ 1], h->phiu,
-            h->flag, h->nx, h->ny, h->tiles_x, h->ntiles, h->model);
-        LBM_CUDA(h, cudaGetLastError());
-        h->cur ^= 1;
-        return LBM_OK;
-    }
     dim3 block(STEP_TX, STEP_TY);
-    dim3 grid((h->nx + STEP_TX - 1) / STEP_TX, (h->ny + STEP_TY - 1) / STEP_TY);
-    if (!fields && h->use_tma16) {
-        auto k = h->prm.storage == LBM_STORE_FP16_SHIFTED
-                     ? (walls ? k_step16_tma<STEP_TX, STEP_TY, ST_FP16, 1>
-                              : k_step16_tma<STEP_TX, STEP_TY, ST_FP16, 0>)
-                     : (walls ? k_step16_tma<STEP_TX, STEP_TY, ST_BF16, 1>
-                              : k_step16_tma<STEP_TX, STEP_TY, ST_BF16, 0>);
-        LBM_CUDA(h, launch_dep(k, grid, block, h->stream, h->tm_w[c], h->tm_f0[c],
-                               (const void*)h->f[c], (const void*)h->g[c], (void*)h->f[c ^ 1],
-                               (void*)h->g[c ^ 1], h->phiu, h->flag, h->nx, h->ny, h->model));
-        h->cur ^= 1;
-        return LBM_OK;
-    }
+    // a 16-bit step's thread takes LBM_NPT16 nodes, so its tile is that many times taller
+    const int th = (!fields && h->prm.storage != LBM_STORE_FP32) ? STEP_TY * LBM_NPT16 : STEP_TY;
+    dim3 grid((h->nx + STEP_TX - 1) / STEP_TX, (h->ny + th - 1) / th);
     using K = void (*)(const float*, const float*, float*, float*, float*, unsigned int*, double*,
                        int, int, Model, int);
     K k;
@@ -725,83 +789,6 @@ static lbm_status check_flag(lbm_handle* h) {
     return LBM_OK;
 }
 
-// Tensor maps over the 3-D arrays [planes][ny][nx] of FP32 (x innermost) for
-// the TMA-staged step.  cuTensorMapEncodeTiled is reached through the runtime's
-// driver entry point so the library needs no link against libcuda.
-// A tensor map over [planes][ny][nx] 32-bit elements (x innermost; planes = 1
-// gives a 2-D map), box [planes][box_y][box_x]: base 16-byte aligned and nx a
-// multiple of 4 (16-byte row pitch), which the callers check.
-static lbm_status encode_map(lbm_handle* h, CUtensorMap* map, void* base, int planes, int box_x,
-                             int box_y, CUtensorMapDataType type = CU_TENSOR_MAP_DATA_TYPE_FLOAT32) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        cudaDriverEntryPointQueryResult q;
-        void* fn = nullptr;
-        LBM_CUDA(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                     cudaEnableDefault, &q));
-        if (q != cudaDriverEntryPointSuccess || !fn)
-            return fail(h, LBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    }
-    if (((uintptr_t)base % 16) != 0 || h->nx % 4 != 0)
-        return fail(h, LBM_ERR_INVALID, "tensor map: base or row pitch not 16-byte aligned");
-    const cuuint32_t rank = planes > 1 ? 3 : 2;
-    const cuuint64_t dims[3] = {(cuuint64_t)h->nx, (cuuint64_t)h->ny, (cuuint64_t)planes};
-    const cuuint64_t strides[2] = {(cuuint64_t)h->nx * 4, (cuuint64_t)h->nx * h->ny * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)planes};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode(map, type, rank, base, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(h, LBM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-    return LBM_OK;
-}
-
-// The 16-bit TMA-staged step: tensor maps over each buffer's 8 word planes
-// (the (f_i, g_i) code pairs) and its f_0 plane.
-static lbm_status setup_tma16(lbm_handle* h) {
-    using T = Tma16Tile<STEP_TX, STEP_TY>;
-    for (int b = 0; b < 2; ++b) {
-        lbm_status st = encode_map(h, &h->tm_w[b], reinterpret_cast<float*>(h->f[b]) + h->N, 8,
-                                   T::BW, T::WH, CU_TENSOR_MAP_DATA_TYPE_UINT32);
-        if (st == LBM_OK) st = encode_map(h, &h->tm_f0[b], h->f[b], 1, T::BW, T::FH);
-        if (st != LBM_OK) return st;
-    }
-    // the kernels hold 12 KB of shared memory per CTA at 9 or 10 CTAs per SM
-    const void* ks[4] = {(const void*)k_step16_tma<STEP_TX, STEP_TY, ST_FP16, 0>,
-                         (const void*)k_step16_tma<STEP_TX, STEP_TY, ST_FP16, 1>,
-                         (const void*)k_step16_tma<STEP_TX, STEP_TY, ST_BF16, 0>,
-                         (const void*)k_step16_tma<STEP_TX, STEP_TY, ST_BF16, 1>};
-    for (const void* k : ks)
-        LBM_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         cudaSharedmemCarveoutMaxShared));
-    h->use_tma16 = true;
-    return LBM_OK;
-}
-
-static lbm_status setup_tma(lbm_handle* h) {
-    for (int b = 0; b < 2; ++b) {
-        lbm_status st = encode_map(h, &h->tm_f[b], h->f[b], 9, TMA_TX + 8, TMA_TY + 4);
-        if (st == LBM_OK) st = encode_map(h, &h->tm_g[b], h->g[b], 9, TMA_TX + 8, TMA_TY + 2);
-        if (st != LBM_OK) return st;
-    }
-    lbm_status st = encode_map(h, &h->tm_u, h->phiu, 2, TMA_TX, TMA_TY);
-    if (st != LBM_OK) return st;
-    LBM_CUDA(h, cudaFuncSetAttribute(k_step_tma<TMA_TX, TMA_TY, TMA_NT, 0>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)TmaCfg::SMEM));
-    LBM_CUDA(h, cudaFuncSetAttribute(k_step_tma<TMA_TX, TMA_TY, TMA_NT, 1>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)TmaCfg::SMEM));
-    int sms = 0;
-    LBM_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    h->tiles_x = (h->nx + TMA_TX - 1) / TMA_TX;
-    h->ntiles = h->tiles_x * ((h->ny + TMA_TY - 1) / TMA_TY);
-    h->tma_grid = h->ntiles < sms ? h->ntiles : sms;
-    h->use_tma = true;
-    return LBM_OK;
-}
-
 extern "C" {
 
 // Shared by lbm_create (ws == NULL: the handle allocates its buffers) and
@@ -831,11 +818,17 @@ static lbm_status create_handle(int nx, int ny, const lbm_params* p, void* ws, l
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     int sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    h->pf_ahead = LBM_PREFETCH_PER10SM * sms / 10;
+    const bool st16 = p->storage != LBM_STORE_FP32;
+    h->pf_ahead = (st16 ? LBM_PREFETCH16_PER10SM : LBM_PREFETCH_PER10SM) * sms / 10;
     {
-        // on grids of a few waves the prefetched tile is often already running
-        const long long tiles = (long long)((nx + STEP_TX - 1) / STEP_TX) * ((ny + STEP_TY - 1) / STEP_TY);
-        if (tiles < (long long)LBM_PREFETCH_MIN_TILES_X * h->pf_ahead) h->pf_ahead = 0;
+        // The prefetch pays only when a step's traffic does not fit in L2:
+        // below, the rows it asks for are mostly there already and the requests
+        // only cost issue slots (measured: FP16 on the 2400 x 600 impact, 132 MB
+        // per step against a 129 MB L2, 48.7 k MLUPS without and 43.7 k with).
+        int l2 = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device);
+        const double bytes = (st16 ? 92.0 : 160.0) * (double)nx * ny;
+        if (bytes * 10.0 < (double)LBM_PREFETCH_L2X10 * l2) h->pf_ahead = 0;
     }
     if (e != cudaSuccess) {
         fprintf(stderr, "lbm_create: %s\n", cudaGetErrorString(e));
@@ -843,28 +836,6 @@ static lbm_status create_handle(int nx, int ny, const lbm_params* p, void* ws, l
         delete h;
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
-    }
-    // LBM_KERNEL_AUTO takes the direct-load kernel: on GB300 it measured 110 us
-    // per 2048^2 step (with L2 prefetch; 128 us without) against 201 us for the
-    // TMA-staged one
-    // the 16-bit staged kernel's box (40 x 8) fits in the grid
-    const bool tma16_ok = p->storage != LBM_STORE_FP32 && nx % 4 == 0 && nx >= 40 && ny >= 8;
-    if (tma16_ok && (p->kernel == LBM_KERNEL_TMA || (p->kernel == LBM_KERNEL_AUTO && LBM_AUTO_TMA16))) {
-        lbm_status ts = setup_tma16(h);
-        if (ts != LBM_OK) {
-            fprintf(stderr, "lbm_create: %s\n", h->err);
-            release(h);
-            delete h;
-            return ts;
-        }
-    } else if (p->kernel == LBM_KERNEL_TMA) {
-        lbm_status ts = setup_tma(h);
-        if (ts != LBM_OK) {
-            fprintf(stderr, "lbm_create: %s\n", h->err);
-            release(h);
-            delete h;
-            return ts;
-        }
     }
     *out = h;
     return LBM_OK;
@@ -1263,28 +1234,48 @@ static_assert(sizeof(BatchTable) <= 32000, "kernel parameters are limited to 32 
 #ifndef LBM_BATCH_THREADS
 #define LBM_BATCH_THREADS 1280
 #endif
+// nodes per thread of the batched 16-bit kernels (their tiles are this many
+// times taller than the thread block)
+#ifndef LBM_NPT16_BATCH
+#define LBM_NPT16_BATCH 2
+#endif
+// resident threads per SM the batched 16-bit kernels are compiled for: 1024 =
+// 8 blocks of 32 x 4 threads, 64 registers (two nodes per thread)
+#ifndef LBM_BATCH_THREADS16
+#define LBM_BATCH_THREADS16 1024
+#endif
 
 // One time step of every case of one boundary class (WALLS = 0: periodic in
 // y, 1: walls in y): block t runs tile t of the class's tile list, whose
 // entry holds (case, tile row << 16 | tile column).
 template <int TX, int TY, int ST, int WALLS>
-__global__ void __launch_bounds__(TX* TY, LBM_BATCH_THREADS / (TX * TY))
+__global__ void __launch_bounds__(TX* TY, (ST == ST_FP32 ? LBM_BATCH_THREADS : LBM_BATCH_THREADS16) /
+                                              (TX * TY))
     k_step_batch(const __grid_constant__ BatchTable T, const int2* __restrict__ tiles, int parity) {
-    __shared__ float sphi[TY + 2][TX + 2];
+    __shared__ float sphi[TY * (ST == ST_FP32 ? 1 : LBM_NPT16_BATCH) + 2][TX + 2];
+    griddep_wait();
+    griddep_launch();
     const int2 e = __ldg(tiles + blockIdx.x);
 #if LBM_DEBUG_CHECKS
     if (e.x < 0 || e.x >= T.ncases || (e.y & 0xffff) * TX >= T.c[e.x < 0 || e.x >= T.ncases ? 0 : e.x].nx ||
-        (e.y >> 16) * TY >= T.c[e.x < 0 || e.x >= T.ncases ? 0 : e.x].ny) {
+        (e.y >> 16) * TY * (ST == ST_FP32 ? 1 : LBM_NPT16_BATCH) >=
+            T.c[e.x < 0 || e.x >= T.ncases ? 0 : e.x].ny) {
         if (e.x >= 0 && e.x < T.ncases) atomicOr(T.c[e.x].flag, 4u);
         else atomicOr(T.c[0].flag, 4u);
         return;  // the whole block leaves before its barrier
     }
 #endif
     const CaseDesc& cd = T.c[e.x];
-    const int x0 = (e.y & 0xffff) * TX, y0 = (e.y >> 16) * TY;
     const int c = (cd.cur + parity) & 1;
-    step_tile<TX, TY, false, WALLS, ST>(sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu,
-                                        cd.flag, nullptr, cd.nx, cd.ny, cd.m, x0, y0);
+    if constexpr (ST == ST_FP32) {
+        step_tile<TX, TY, false, WALLS, ST>(sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu,
+                                            cd.flag, nullptr, cd.nx, cd.ny, cd.m, (e.y & 0xffff) * TX,
+                                            (e.y >> 16) * TY);
+    } else {
+        step_tile16<TX, TY, LBM_NPT16_BATCH, WALLS, ST>(
+            sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu, cd.flag, cd.nx, cd.ny, cd.m,
+            (e.y & 0xffff) * TX, (e.y >> 16) * TY * LBM_NPT16_BATCH);
+    }
 }
 
 // boundary classes: each has its own specialised kernel, stream and tile shape
@@ -1418,9 +1409,10 @@ static void batch_sync_table(lbm_batch* b) {
 static lbm_status batch_launch(lbm_batch* b, int cls, int cand, int parity) {
     BatchKernel k = batch_kernel_for(b->storage, cls, cand);
     const BatchTable& T = b->tab(cls, cand);
-    k<<<T.tile0[T.ncases], dim3(BATCH_TX[cand], BATCH_TY[cand]), 0, b->bs[cls]>>>(
-        T, b->d_tiles[cls * BATCH_NCAND + cand], parity);
-    LBM_BCUDA(b, cudaGetLastError());
+    // programmatic dependent launch, as for the single-case steps (also inside
+    // the captured graph, where it becomes a programmatic edge)
+    LBM_BCUDA(b, launch_dep(k, dim3(T.tile0[T.ncases]), dim3(BATCH_TX[cand], BATCH_TY[cand]),
+                            b->bs[cls], T, (const int2*)b->d_tiles[cls * BATCH_NCAND + cand], parity));
     return LBM_OK;
 }
 
@@ -1589,6 +1581,8 @@ lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** ou
         for (int k = 0; k < BATCH_NCAND; ++k) {
             BatchTable& T = b->tab(cls, k);
             memset(&T, 0, sizeof T);
+            // tile height in nodes (16-bit kernels take LBM_NPT16_BATCH nodes per thread)
+            const int th = BATCH_TY[k] * (b->storage == LBM_STORE_FP32 ? 1 : LBM_NPT16_BATCH);
             T.ncases = b->ncls[cls];
             long long tiles = 0;
             for (int c = 0; c < ncases; ++c) {
@@ -1608,7 +1602,7 @@ lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** ou
                 d.m = h->model;
                 T.tiles_x[j] = (h->nx + BATCH_TX[k] - 1) / BATCH_TX[k];
                 T.tile0[j] = (int)tiles;
-                tiles += (long long)T.tiles_x[j] * ((h->ny + BATCH_TY[k] - 1) / BATCH_TY[k]);
+                tiles += (long long)T.tiles_x[j] * ((h->ny + th - 1) / th);
             }
             if (tiles >= (1LL << 31) - 1) {
                 bfail(b, LBM_ERR_INVALID, "batch too large for one launch");
@@ -1619,7 +1613,7 @@ lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** ou
             std::vector<int2> list((size_t)tiles);
             size_t n = 0;
             for (int j = 0; j < T.ncases; ++j) {
-                const int tx = T.tiles_x[j], ty = (T.c[j].ny + BATCH_TY[k] - 1) / BATCH_TY[k];
+                const int tx = T.tiles_x[j], ty = (T.c[j].ny + th - 1) / th;
                 if (tx > 0xffff || ty > 0x7fff) {
                     bfail(b, LBM_ERR_INVALID, "a case has more than 65535 x 32767 tiles");
                     return bad(LBM_ERR_INVALID);
@@ -1677,7 +1671,8 @@ lbm_status lbm_batch_info(const lbm_batch* b, int cls, int* ncases, int* tile_tx
     if (!b || cls < 0 || cls >= BATCH_NCLASS) return LBM_ERR_INVALID;
     if (ncases) *ncases = b->ncls[cls];
     if (tile_tx) *tile_tx = BATCH_TX[b->cand[cls]];
-    if (tile_ty) *tile_ty = BATCH_TY[b->cand[cls]];
+    if (tile_ty)
+        *tile_ty = BATCH_TY[b->cand[cls]] * (b->storage == LBM_STORE_FP32 ? 1 : LBM_NPT16_BATCH);
     if (us_per_step) *us_per_step = b->tuned_us[cls][b->cand[cls]];
     if (tuned) *tuned = b->tuned ? 1 : 0;
     return LBM_OK;
@@ -1911,29 +1906,6 @@ __global__ void __launch_bounds__(RED_THREADS)
 }  // namespace
 
 extern "C" {
-
-lbm_status lbm_selftest_bounded_wait(void* stream, int* timed_out) {
-    if (!timed_out) return LBM_ERR_INVALID;
-    *timed_out = 0;
-    cudaStream_t s = (cudaStream_t)stream;
-    unsigned int* d = nullptr;
-    unsigned int v = 0;
-    cudaError_t e = cudaMalloc(&d, sizeof v);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof v, s);
-    if (e == cudaSuccess) {
-        k_wait_selftest<<<1, 32, 0, s>>>(d, 4096);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, d, sizeof v, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(d);
-    if (e != cudaSuccess) {
-        fprintf(stderr, "lbm_selftest_bounded_wait: %s\n", cudaGetErrorString(e));
-        return LBM_ERR_CUDA;
-    }
-    *timed_out = (v & 2u) ? 1 : 0;
-    return LBM_OK;
-}
 
 lbm_status lbm_laplace_jump(lbm_handle* h, double xc, double yc, double r_in, double r_out,
                             double* dp) {

@@ -254,8 +254,9 @@ struct Pop<ST_BF16> : Shifted16<__nv_bfloat16> {};
 // codes.  With V as in collide, (f_i^eq + tau_f F_i) / w_i - 1/2 =
 // phi - 1/2 + 3 c_i . V and (g_i^eq + tau_g G_i) GS / w_i = GS (rho s_i / w_i
 // + 3 nu [3 c_i . F + 3 (rho_l - rho_g)(c_i . u)(c_i . grad phi)] + 3 p) for
-// i > 0, GS (rho s_0 / w_0 + 3 p (w_0 - 1) / w_0) for i = 0.  f_0 is not
-// collided: the store writes it as the remainder.  Returns (phi ux, phi uy).
+// i > 0, GS (rho s_0 / w_0 + 3 p (w_0 - 1) / w_0) for i = 0, with s_i / w_i =
+// 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 |u|^2.  f_0 is not collided: the store writes
+// it as the remainder.  Returns (phi ux, phi uy).
 template <class P>
 __device__ __forceinline__ float2 collide_code(const Model& m, float h[9], float k[9], float phi,
                                                const Stencil& st, const Macro& M, float2 phiu_prev) {
@@ -318,12 +319,20 @@ __device__ __forceinline__ float2 collide_code(const Model& m, float h[9], float
         const float ke0 = fma_rn(rho, m15, mul(p3, (w_of(0) - 1.f) / w_of(0)));
         k[0] = fma_rn(omega_g, sub(ke0, k[0]), k[0]);
     }
+    // Opposite directions i, o(i) share the part of the target even in c_i,
+    // A = rho (4.5 (c_i.u)^2 - 1.5 |u|^2) + (c_i.u)(c_i . 3 nu 3 (rho_l -
+    // rho_g) grad phi) + 3p, and take the odd part B = 3 rho c_i.u + c_i . 3 nu
+    // 3F with opposite signs: A + B and A - B.
+    const float rho3 = mul(3.f, rho);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
-        const float s = fma_rn(cu[i], fma_rn(4.5f, cu[i], 3.f), m15);   // s_i / w_i
-        const float t = add(fma_rn(cu[i], ce[i], ch[i]), p3);
-        const float ke = fma_rn(rho, s, t);
-        k[i] = fma_rn(omega_g, sub(ke, k[i]), k[i]);
+        if (i == 3 || i == 4 || i == 7 || i == 8) continue;  // done with its opposite
+        const int o = opp_of(i);
+        const float c = cu[i];
+        const float A = fma_rn(rho, fma_rn(mul(4.5f, c), c, m15), fma_rn(c, ce[i], p3));
+        const float B = fma_rn(rho3, c, ch[i]);
+        k[i] = fma_rn(omega_g, sub(add(A, B), k[i]), k[i]);
+        k[o] = fma_rn(omega_g, sub(sub(A, B), k[o]), k[o]);
     }
     return phiu;
 }
@@ -338,22 +347,23 @@ __device__ __forceinline__ float2 collide_st(const Model& m, float f[9], float g
         return collide_code<Pop<ST>>(m, f, g, phi, st, M, prev);
 }
 
-// Pull (stream) node q through a 16-bit storage format: the nine loads first
-// (f_0 and g_0, and one word of (f_i, g_i) codes per moving direction), then
-// the conversions of the codes to FP32 (f[0] is the FP32 value of f_0,
-// f[1..8] and g[0..8] are the codes h_i and k_i).  The six wall-dependent
-// loads sit in a branch that is uniform across a warp (BR; a warp covers part
-// of one tile row), or are per-lane selects.  G: convert g as well.
+// Pull (stream) node q through a 16-bit storage format: the nine loads (f_0
+// and g_0, and one word of (f_i, g_i) codes per moving direction; w[i] holds
+// direction i's word).  The six wall-dependent loads sit in a branch that is
+// uniform across a warp (BR; a warp covers part of one tile row), or are
+// per-lane selects.  G: load g_0 as well.  pull_16 adds the conversions of
+// the codes to FP32 (f[0] is the FP32 value of f_0, f[1..8] and g[0..8] the
+// codes h_i and k_i).
 template <int ST, bool BR, bool G>
-__device__ __forceinline__ void pull_16(const void* fs, const void* gs, int N, const Nbr& q,
-                                        float f[9], float g[9]) {
+__device__ __forceinline__ void pull_words16(const void* fs, const void* gs, int N, const Nbr& q,
+                                             unsigned int w[9], float& f0, unsigned short& g0) {
     using P = Pop<ST>;
     const unsigned int* W = P::pw(fs, N);
     auto raw = [&](int i, int idx) { return __ldg(W + ((i - 1) * N + idx)); };
-    unsigned int w[9];
-    const float f0 = __ldg(static_cast<const float*>(fs) + (q.r0 + q.x));
-    unsigned short g0 = 0;
+    f0 = __ldg(static_cast<const float*>(fs) + (q.r0 + q.x));
+    g0 = 0;
     if (G) g0 = __ldg(static_cast<const unsigned short*>(gs) + (q.r0 + q.x));
+    w[0] = 0u;
     w[1] = raw(1, q.r0 + q.xm);
     w[3] = raw(3, q.r0 + q.xp);
     if (!BR || q.lo || q.hi) {
@@ -371,17 +381,36 @@ __device__ __forceinline__ void pull_16(const void* fs, const void* gs, int N, c
         w[7] = raw(7, q.rp + q.xp);
         w[8] = raw(8, q.rp + q.xm);
     }
-    // the codes as floats; a bounce-back link takes the code of the stored
-    // direction, which has the pulled direction's weight (opposite directions
-    // share w_i), so the code means the same population in either
-    f[0] = f0;
+}
+
+// the codes as floats: h[0] = f_0 (an FP32 value), h[1..8] the f codes; k[0..8]
+// the g codes.  A bounce-back link takes the code of the stored direction,
+// which has the pulled direction's weight (opposite directions share w_i), so
+// the code means the same population in either.
+template <int ST>
+__device__ __forceinline__ void codes_f(const unsigned int w[9], float f0, float h[9]) {
+    using P = Pop<ST>;
+    h[0] = f0;
 #pragma unroll
-    for (int i = 1; i < 9; ++i) f[i] = P::C::to_f(P::lo(w[i]));
-    if (G) {
-        g[0] = P::C::to_f(g0);
+    for (int i = 1; i < 9; ++i) h[i] = P::C::to_f(P::lo(w[i]));
+}
+template <int ST>
+__device__ __forceinline__ void codes_g(const unsigned int w[9], unsigned short g0, float k[9]) {
+    using P = Pop<ST>;
+    k[0] = P::C::to_f(g0);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) g[i] = P::C::to_f(P::hi(w[i]));
-    }
+    for (int i = 1; i < 9; ++i) k[i] = P::C::to_f(P::hi(w[i]));
+}
+
+template <int ST, bool BR, bool G>
+__device__ __forceinline__ void pull_16(const void* fs, const void* gs, int N, const Nbr& q,
+                                        float f[9], float g[9]) {
+    unsigned int w[9];
+    float f0;
+    unsigned short g0;
+    pull_words16<ST, BR, G>(fs, gs, N, q, w, f0, g0);
+    codes_f<ST>(w, f0, f);
+    if (G) codes_g<ST>(w, g0, g);
 }
 
 // Pull both population sets of node q in any storage format (WALLS as in

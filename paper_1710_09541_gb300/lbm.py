@@ -26,7 +26,7 @@ LBM_VISC_LINEAR_NU, LBM_VISC_INVERSE_NU, LBM_VISC_STEP_MU = 0, 1, 2
 LBM_BC_PERIODIC, LBM_BC_WALLS, LBM_BC_WALL_OPEN = 0, 1, 2
 LBM_NORMAL_CENTRAL, LBM_NORMAL_LOCAL = 0, 1
 LBM_STORE_FP32, LBM_STORE_FP16_SHIFTED, LBM_STORE_BF16_SHIFTED = 0, 1, 2
-LBM_KERNEL_AUTO, LBM_KERNEL_GENERIC, LBM_KERNEL_TMA = 0, 1, 2
+LBM_KERNEL_AUTO, LBM_KERNEL_GENERIC = 0, 1
 
 # every entry point include/lbm_pf.h declares
 EXPORTS = ("lbm_create", "lbm_init", "lbm_step", "lbm_get_fields", "lbm_state_bytes",
@@ -34,7 +34,7 @@ EXPORTS = ("lbm_create", "lbm_init", "lbm_step", "lbm_get_fields", "lbm_state_by
            "lbm_last_error", "lbm_diag_fields_noalloc", "lbm_batch_create", "lbm_batch_step",
            "lbm_batch_info", "lbm_batch_destroy", "lbm_batch_last_error",
            "lbm_spreading_radius", "lbm_probe", "lbm_workspace_bytes", "lbm_create_in",
-           "lbm_laplace_jump", "lbm_selftest_bounded_wait")
+           "lbm_laplace_jump")
 
 
 class LbmError(RuntimeError):
@@ -87,7 +87,6 @@ def load() -> ctypes.CDLL:
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_diag_fields_noalloc.argtypes = [vp, sz, vp, vp, ctypes.c_char_p, sz]
     L.lbm_spreading_radius.argtypes = [vp, i, i, pd, pd]
-    L.lbm_selftest_bounded_wait.argtypes = [vp, ctypes.POINTER(i)]
     L.lbm_laplace_jump.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, pd]
     L.lbm_workspace_bytes.argtypes = [i, i, ctypes.POINTER(lbm_params), ctypes.POINTER(sz)]
@@ -144,18 +143,6 @@ def diag_fields_noalloc(d_fields: int, n: int, d_out: int, stream=None) -> None:
 
 def _dptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-
-
-def selftest_bounded_wait(stream=None) -> bool:
-    """lbm_selftest_bounded_wait: True when the bounded wait gave up as it should."""
-    L = load()
-    if stream is not None and hasattr(stream, "cuda_stream"):
-        stream = stream.cuda_stream
-    t = ctypes.c_int()
-    rc = L.lbm_selftest_bounded_wait(stream or None, ctypes.byref(t))
-    if rc != LBM_OK:
-        raise LbmError(rc, "lbm_selftest_bounded_wait failed (see stderr)")
-    return bool(t.value)
 
 
 def workspace_bytes(nx: int, ny: int, **params) -> int:

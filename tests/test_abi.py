@@ -114,7 +114,7 @@ def test_header_enum_values_match_the_binding():
     text = open(os.path.join(ROOT, "include", "lbm_pf.h")).read()
     for name in ("LBM_BC_PERIODIC", "LBM_BC_WALLS", "LBM_BC_WALL_OPEN", "LBM_STORE_FP32",
                  "LBM_STORE_FP16_SHIFTED", "LBM_STORE_BF16_SHIFTED", "LBM_KERNEL_AUTO",
-                 "LBM_KERNEL_GENERIC", "LBM_KERNEL_TMA"):
+                 "LBM_KERNEL_GENERIC"):
         m = re.search(name + r"\s*=\s*(\d+)", text)
         assert m and int(m.group(1)) == getattr(lbm, name), name
 

@@ -481,53 +481,3 @@ def test_poiseuille_steady_state_fp32_vs_fp64_and_eq31(lbm):
     assert rel < 2.5e-3, (rel, drift)
     assert l2(ug) < 1.05 * l2(uo) + 1e-3, (l2(ug), l2(uo))
     assert abs(drift) < 1e-5
-
-
-# ------------------------------------------------------------ kernels ------
-
-@pytest.mark.parametrize("nx,ny,bc", [(128, 96, 0), (100, 70, 0), (200, 45, 1), (72, 20, 0), (300, 37, 1)])
-def test_step_kernels_agree_bitwise(lbm, nx, ny, bc):
-    """The direct-load (LBM_KERNEL_GENERIC) and TMA-staged (LBM_KERNEL_TMA)
-    steps evaluate the same formulas on the same values: their states after
-    50 steps agree bit for bit, on periodic, ragged and walled grids,
-    including tiles on the periodic seams."""
-    P = dict(rho_l=1.0, rho_g=0.01, nu_l=0.05, nu_g=0.15, visc_mode=1, sigma=5e-3, W=4.0,
-             tau_h=0.7, Gx=2e-6, Gy=-1e-6, bc_y=bc)
-    # a small drop centred on the periodic seam (all its periodic images), so
-    # the tiles at the seam carry interface in their wrapped halo
-    seam = [cases.drop(nx, ny, 6, 4.0, x0=2 + ix * nx, y0=ny / 2 + iy * ny, walls_y=bool(bc))
-            for ix in (-1, 0, 1) for iy in ((0,) if bc else (-1, 0, 1))]
-    phi0 = np.maximum(cases.drop(nx, ny, min(nx, ny) / 4, 4.0, x0=0.6 * nx, walls_y=bool(bc)),
-                      np.max(seam, axis=0))
-    u0 = 1e-3 * np.sin(np.arange(nx) / 5.0)[None, :] * np.ones((ny, 1))
-    states = []
-    for kernel in (lbm.LBM_KERNEL_GENERIC, lbm.LBM_KERNEL_TMA):
-        with lbm.Lattice(nx, ny, kernel=kernel, **P) as g:
-            states.append(g.init(phi0, u0, -u0).step(50).get_state())
-    for other in states[1:]:
-        for a, b in zip(states[0], other):
-            assert np.array_equal(a, b), float(np.abs(a - b).max())
-
-
-@pytest.mark.parametrize("storage", [1, 2])
-@pytest.mark.parametrize("nx,ny,bc", [(128, 96, 0), (100, 70, 0), (200, 45, 1), (40, 8, 0), (300, 37, 2),
-                                      (72, 20, 1), (44, 9, 2)])
-def test_16bit_step_kernels_agree_bitwise(lbm, storage, nx, ny, bc):
-    """With 16-bit storage the TMA-staged kernel (one tile per CTA, pulls from
-    shared memory, periodic seams patched from global memory) and the
-    direct-load kernel give the same bits after 50 steps, on periodic, walled
-    and open-top grids, ragged and as small as the staged box."""
-    P = dict(rho_l=1.0, rho_g=0.01, nu_l=0.05, nu_g=0.15, visc_mode=1, sigma=5e-3, W=4.0,
-             tau_h=0.7, Gx=2e-6, Gy=-1e-6, bc_y=bc, storage=storage)
-    walls = bc > 0
-    seam = [cases.drop(nx, ny, 6, 4.0, x0=2 + ix * nx, y0=ny / 2 + iy * ny, walls_y=walls)
-            for ix in (-1, 0, 1) for iy in ((0,) if walls else (-1, 0, 1))]
-    phi0 = np.maximum(cases.drop(nx, ny, min(nx, ny) / 4, 3.0, x0=0.6 * nx, walls_y=walls),
-                      np.max(seam, axis=0))
-    u0 = 1e-3 * np.sin(np.arange(nx) / 5.0)[None, :] * np.ones((ny, 1))
-    states = []
-    for kernel in (lbm.LBM_KERNEL_GENERIC, lbm.LBM_KERNEL_TMA):
-        with lbm.Lattice(nx, ny, kernel=kernel, **P) as g:
-            states.append(g.init(phi0, u0, -u0).step(50).get_state())
-    for a, b in zip(*states):
-        assert np.array_equal(a, b), float(np.abs(a - b).max())

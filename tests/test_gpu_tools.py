@@ -138,14 +138,3 @@ def test_laplace_jump_resolved_drop_vs_oracle(lbm):
             ref.append(_jump_host(o.fields()["p"], n / 2, n / 2, R / 2, R + 12, True))
     assert abs(np.mean(got) / np.mean(ref) - 1) < 0.01
     assert abs(np.mean(got) * R / 0.01 - 1) < 0.03
-
-
-def test_bounded_wait_gives_up_and_device_stays_usable(lbm):
-    """The staged kernel's bounded mbarrier wait, on a barrier no copy will
-    complete, gives up and reports it (twice in a row); afterwards a lattice
-    steps normally on the same context."""
-    assert lbm.selftest_bounded_wait() is True
-    assert lbm.selftest_bounded_wait() is True
-    with lbm.Lattice(32, 32, **cases.params_static_drop()) as g:
-        g.init(cases.drop(32, 32, 8, 4.0)).step(10)
-        assert np.isfinite(g.diag()[0])
