@@ -151,6 +151,9 @@ __device__ __forceinline__ void griddep_launch() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+#ifndef LBM_FLAG_READ_FIRST
+#define LBM_FLAG_READ_FIRST 0
+#endif
 // Record a non-finite node in the status flag with one atomic per warp: the
 // lowest lane of those that reach this call (the offending ones) reports for
 // all of them, so a blown-up state does not serialise on one address.
@@ -158,7 +161,12 @@ __device__ __forceinline__ void report_nonfinite(unsigned int* flag) {
     const unsigned int lanes = __activemask();
     unsigned int lane;
     asm("mov.u32 %0, %%laneid;" : "=r"(lane));
+#if LBM_FLAG_READ_FIRST
+    // once the bit is set, later warps read it (from L2) instead of queueing atomics
+    if (lane == (unsigned int)(__ffs(lanes) - 1) && !(__ldcg(flag) & 1u)) atomicOr(flag, 1u);
+#else
     if (lane == (unsigned int)(__ffs(lanes) - 1)) atomicOr(flag, 1u);
+#endif
 }
 
 // c_i . v for the nine directions of Eq. 10; opposite directions get exactly

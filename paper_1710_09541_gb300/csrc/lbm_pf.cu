@@ -1234,6 +1234,10 @@ static_assert(sizeof(BatchTable) <= 32000, "kernel parameters are limited to 32 
 #ifndef LBM_BATCH_THREADS
 #define LBM_BATCH_THREADS 1280
 #endif
+// L2 prefetch distance of the batched kernels, in tiles per 10 SMs (0: off)
+#ifndef LBM_BATCH_PF_PER10SM
+#define LBM_BATCH_PF_PER10SM 20
+#endif
 // nodes per thread of the batched 16-bit kernels (their tiles are this many
 // times taller than the thread block)
 #ifndef LBM_NPT16_BATCH
@@ -1251,10 +1255,21 @@ static_assert(sizeof(BatchTable) <= 32000, "kernel parameters are limited to 32 
 template <int TX, int TY, int ST, int WALLS>
 __global__ void __launch_bounds__(TX* TY, (ST == ST_FP32 ? LBM_BATCH_THREADS : LBM_BATCH_THREADS16) /
                                               (TX * TY))
-    k_step_batch(const __grid_constant__ BatchTable T, const int2* __restrict__ tiles, int parity) {
+    k_step_batch(const __grid_constant__ BatchTable T, const int2* __restrict__ tiles, int parity,
+                 int pf_ahead) {
     __shared__ float sphi[TY * (ST == ST_FP32 ? 1 : LBM_NPT16_BATCH) + 2][TX + 2];
     griddep_wait();
     griddep_launch();
+    constexpr int TH = TY * (ST == ST_FP32 ? 1 : LBM_NPT16_BATCH);  // tile height in nodes
+    // L2 prefetch of the tile pf_ahead entries later in the list, as in the
+    // single-case step (0: off)
+    if (pf_ahead > 0 && blockIdx.x + pf_ahead < gridDim.x) {
+        const int2 pe = __ldg(tiles + blockIdx.x + pf_ahead);
+        const CaseDesc& pc = T.c[pe.x < T.ncases ? pe.x : 0];
+        const int pcur = (pc.cur + parity) & 1;
+        prefetch_tile<TX, TH, TX * TY, ST>(pc.f[pcur], pc.g[pcur], pc.phiu, pc.nx, pc.ny, WALLS,
+                                           pe.y & 0xffff, pe.y >> 16);
+    }
     const int2 e = __ldg(tiles + blockIdx.x);
 #if LBM_DEBUG_CHECKS
     if (e.x < 0 || e.x >= T.ncases || (e.y & 0xffff) * TX >= T.c[e.x < 0 || e.x >= T.ncases ? 0 : e.x].nx ||
@@ -1291,7 +1306,7 @@ constexpr int BATCH_GRAPH_STEPS = 32;  // steps per graph replay (even)
 constexpr int BATCH_TUNE_WARM = 4, BATCH_TUNE_WINDOW = 12, BATCH_TUNE_WINDOWS = 2;
 constexpr int BATCH_TUNE_PER_SHAPE = BATCH_TUNE_WARM + BATCH_TUNE_WINDOW * BATCH_TUNE_WINDOWS;
 
-using BatchKernel = void (*)(BatchTable, const int2*, int);
+using BatchKernel = void (*)(BatchTable, const int2*, int, int);
 
 template <int ST, int W>
 BatchKernel batch_kernel(int cand) {
@@ -1345,6 +1360,7 @@ struct lbm_batch {
     int* d_slot[BATCH_NCLASS] = {};     // per class: the batch index of each class slot
     unsigned int* d_flags = nullptr;    // gathered flags, one per case
     int cand[BATCH_NCLASS] = {1, 1};  // tile shape in use per class (index into BATCH_TX/TY)
+    int pf_ahead = 0;                 // L2 prefetch distance in tiles (0: off)
     bool tuned = false;
     double tuned_us[BATCH_NCLASS][BATCH_NCAND] = {};
     cudaGraphExec_t graph = nullptr;
@@ -1412,7 +1428,8 @@ static lbm_status batch_launch(lbm_batch* b, int cls, int cand, int parity) {
     // programmatic dependent launch, as for the single-case steps (also inside
     // the captured graph, where it becomes a programmatic edge)
     LBM_BCUDA(b, launch_dep(k, dim3(T.tile0[T.ncases]), dim3(BATCH_TX[cand], BATCH_TY[cand]),
-                            b->bs[cls], T, (const int2*)b->d_tiles[cls * BATCH_NCAND + cand], parity));
+                            b->bs[cls], T, (const int2*)b->d_tiles[cls * BATCH_NCAND + cand], parity,
+                            b->pf_ahead));
     return LBM_OK;
 }
 
@@ -1634,6 +1651,16 @@ lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** ou
     for (int c = 0; c < ncases; ++c) {
         b->node_count += (long long)cases[c]->N;
         if (cases[c]->prm.check_every > 0) b->check = true;
+    }
+    {
+        // prefetch when a step's traffic exceeds the L2 threshold of the
+        // single-case step (the classes run concurrently: their sum counts)
+        int sms = 0, l2 = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess &&
+            cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device) == cudaSuccess) {
+            const double bytes = (b->storage == LBM_STORE_FP32 ? 160.0 : 92.0) * (double)b->node_count;
+            if (bytes * 10.0 >= (double)LBM_PREFETCH_L2X10 * l2) b->pf_ahead = LBM_BATCH_PF_PER10SM * sms / 10;
+        }
     }
     // batch index of each class slot, for gathering the cases' flags
     for (int cls = 0; cls < BATCH_NCLASS; ++cls) {
