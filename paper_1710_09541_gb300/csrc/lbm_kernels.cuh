@@ -50,6 +50,7 @@ struct Model {
     int walls;              // y boundary: 0 periodic, 1 bounce-back walls at both
                             // ends, 2 bounce-back wall at y = 0 and an open top
     int local_normal;       // Eq. 29 instead of Eq. 2 with Eq. 27
+    int check_nonfinite;    // record non-finite nodes in the status flag (check_every > 0)
 };
 
 // Neighbour addressing of one node: row offsets and wrapped columns.
@@ -152,11 +153,13 @@ __device__ __forceinline__ void griddep_launch() {
 }
 
 #ifndef LBM_FLAG_READ_FIRST
-#define LBM_FLAG_READ_FIRST 0
+#define LBM_FLAG_READ_FIRST 1
 #endif
-// Record a non-finite node in the status flag with one atomic per warp: the
-// lowest lane of those that reach this call (the offending ones) reports for
-// all of them, so a blown-up state does not serialise on one address.
+// Record a non-finite node in the status flag: the lowest lane of those that
+// reach this call (the offending ones) reports for its warp, and only while
+// the bit is not yet set, so a blown-up state does not serialise on one
+// address (measured at 2048^2 with 58% of the nodes NaN: FP32 19.3 k MLUPS with
+// one atomic per warp, 39.3 k with the read first, against 40.4 k healthy).
 __device__ __forceinline__ void report_nonfinite(unsigned int* flag) {
     const unsigned int lanes = __activemask();
     unsigned int lane;

@@ -96,7 +96,7 @@ __device__ __forceinline__ bool nbr_in_range(const Nbr& q, int nx, int ny) {
 #endif
 // One TX x TY tile with origin (x0, y0): the body shared by the single-case
 // step kernel and the batched kernel (so both give the same bits).
-template <int TX, int TY, bool FIELDS, int WALLS, int ST>
+template <int TX, int TY, bool FIELDS, int WALLS, int ST, bool CHK>
 __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __restrict__ fs,
                                           const float* __restrict__ gs, float* __restrict__ fd,
                                           float* __restrict__ gd, float* __restrict__ phiu,
@@ -174,8 +174,10 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
         out[4 * N + n32] = M.p;
         return;
     }
-    // one test: a NaN or Inf in any of phi, u, p makes the sum non-finite
-    if (!isfinite(add(add(phi, M.ux), add(M.uy, M.p)))) report_nonfinite(flag);
+    // one test: a NaN or Inf in any of phi, u, p makes the sum non-finite;
+    // reported after the stores, so the branch does not split the update
+    bool bad = false;
+    if constexpr (CHK) bad = m.check_nonfinite && !isfinite(add(add(phi, M.ux), add(M.uy, M.p)));
 
 #if !LBM_EARLY_PHIU
     const float2 prev = make_float2(phiu[n32], phiu[N32 + n32]);
@@ -184,6 +186,8 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
     phiu[n32] = now.x;
     phiu[N32 + n32] = now.y;
     Pop<ST>::stfg(fd, gd, N32, n32, f, g, phi);
+    if constexpr (CHK)
+        if (bad) report_nonfinite(flag);
 }
 
 // One TX x (NPT TY) tile with 16-bit storage: each of the TX x TY threads
@@ -195,7 +199,7 @@ __device__ __forceinline__ void step_tile(float (*sphi)[TX + 2], const float* __
 #ifndef LBM_NPT16
 #define LBM_NPT16 2
 #endif
-template <int TX, int TY, int NPT, int WALLS, int ST>
+template <int TX, int TY, int NPT, int WALLS, int ST, bool CHK>
 __device__ __forceinline__ void step_tile16(float (*sphi)[TX + 2], const void* __restrict__ fs,
                                             const void* __restrict__ gs, void* __restrict__ fd,
                                             void* __restrict__ gd, float* __restrict__ phiu,
@@ -270,11 +274,14 @@ __device__ __forceinline__ void step_tile16(float (*sphi)[TX + 2], const void* _
                                    sphi[ly - 1][lx], sphi[ly + 1][lx + 1], sphi[ly + 1][lx - 1],
                                    sphi[ly - 1][lx - 1], sphi[ly - 1][lx + 1]);
         const Macro M = macro_from(m, Pop<ST>::gmom(k), phi, st.gx, st.gy, st.lap);
-        if (!isfinite(add(add(phi, M.ux), add(M.uy, M.p)))) report_nonfinite(flag);
+        bool bad = false;
+        if constexpr (CHK) bad = m.check_nonfinite && !isfinite(add(add(phi, M.ux), add(M.uy, M.p)));
         const float2 now = collide_code<Pop<ST>>(m, h, k, phi, st, M, prev[j]);
         phiu[n[j]] = now.x;
         phiu[N + n[j]] = now.y;
         Pop<ST>::stfg(fd, gd, N, n[j], h, k, phi);
+        if constexpr (CHK)
+            if (bad) report_nonfinite(flag);
     }
 }
 
@@ -330,7 +337,7 @@ __host__ __device__ constexpr int step_npt() {
     return (!FIELDS && ST != ST_FP32) ? LBM_NPT16 : 1;
 }
 
-template <int TX, int TY, bool FIELDS, int WALLS, int ST>
+template <int TX, int TY, bool FIELDS, int WALLS, int ST, bool CHK = false>
 __global__ void __launch_bounds__(TX* TY, (step_minb<FIELDS, WALLS, ST>()))
     k_step(const float* __restrict__ fs, const float* __restrict__ gs, float* __restrict__ fd,
            float* __restrict__ gd, float* __restrict__ phiu, unsigned int* __restrict__ flag,
@@ -356,10 +363,10 @@ __global__ void __launch_bounds__(TX* TY, (step_minb<FIELDS, WALLS, ST>()))
         }
     }
     if constexpr (NPT > 1 || (!FIELDS && ST != ST_FP32))
-        step_tile16<TX, TY, NPT, WALLS, ST>(sphi, fs, gs, fd, gd, phiu, flag, nx, ny, m,
+        step_tile16<TX, TY, NPT, WALLS, ST, CHK>(sphi, fs, gs, fd, gd, phiu, flag, nx, ny, m,
                                             blockIdx.x * TX, blockIdx.y * TY * NPT);
     else
-        step_tile<TX, TY, FIELDS, WALLS, ST>(sphi, fs, gs, fd, gd, phiu, flag, out, nx, ny, m,
+        step_tile<TX, TY, FIELDS, WALLS, ST, CHK>(sphi, fs, gs, fd, gd, phiu, flag, out, nx, ny, m,
                                              blockIdx.x * TX, blockIdx.y * TY);
 }
 
@@ -661,6 +668,7 @@ static Model make_model(const lbm_params& p) {
     m.visc_mode = p.visc_mode;
     m.walls = p.bc_y;  // 0 periodic, 1 walls, 2 wall and open top
     m.local_normal = p.normal_scheme == LBM_NORMAL_LOCAL;
+    m.check_nonfinite = p.check_every > 0;
     return m;
 }
 
@@ -745,22 +753,21 @@ static lbm_status launch_step(lbm_handle* h, bool fields, double* out) {
     using K = void (*)(const float*, const float*, float*, float*, float*, unsigned int*, double*,
                        int, int, Model, int);
     K k;
+    // the steps of a handle that asked for non-finite checks test every node;
+    // the others are compiled without the test (2% of the 16-bit step)
+    const bool chk = h->model.check_nonfinite != 0;
+#define LBM_STEP_KERNEL(ST_)                                                                      \
+    (fields ? k_step<STEP_TX, STEP_TY, true, -1, ST_>                                            \
+            : (walls ? (chk ? k_step<STEP_TX, STEP_TY, false, 1, ST_, true>                      \
+                            : k_step<STEP_TX, STEP_TY, false, 1, ST_, false>)                    \
+                     : (chk ? k_step<STEP_TX, STEP_TY, false, 0, ST_, true>                      \
+                            : k_step<STEP_TX, STEP_TY, false, 0, ST_, false>)))
     switch (h->prm.storage) {
-        case LBM_STORE_FP16_SHIFTED:
-            k = fields ? k_step<STEP_TX, STEP_TY, true, -1, ST_FP16>
-                       : (walls ? k_step<STEP_TX, STEP_TY, false, 1, ST_FP16>
-                                : k_step<STEP_TX, STEP_TY, false, 0, ST_FP16>);
-            break;
-        case LBM_STORE_BF16_SHIFTED:
-            k = fields ? k_step<STEP_TX, STEP_TY, true, -1, ST_BF16>
-                       : (walls ? k_step<STEP_TX, STEP_TY, false, 1, ST_BF16>
-                                : k_step<STEP_TX, STEP_TY, false, 0, ST_BF16>);
-            break;
-        default:
-            k = fields ? k_step<STEP_TX, STEP_TY, true, -1, ST_FP32>
-                       : (walls ? k_step<STEP_TX, STEP_TY, false, 1, ST_FP32>
-                                : k_step<STEP_TX, STEP_TY, false, 0, ST_FP32>);
+        case LBM_STORE_FP16_SHIFTED: k = LBM_STEP_KERNEL(ST_FP16); break;
+        case LBM_STORE_BF16_SHIFTED: k = LBM_STEP_KERNEL(ST_BF16); break;
+        default: k = LBM_STEP_KERNEL(ST_FP32);
     }
+#undef LBM_STEP_KERNEL
     if (fields)
         k<<<grid, block, 0, h->stream>>>(h->f[c], h->g[c], nullptr, nullptr, h->phiu, h->flag, out,
                                          h->nx, h->ny, h->model, 0);
@@ -1252,7 +1259,7 @@ static_assert(sizeof(BatchTable) <= 32000, "kernel parameters are limited to 32 
 // One time step of every case of one boundary class (WALLS = 0: periodic in
 // y, 1: walls in y): block t runs tile t of the class's tile list, whose
 // entry holds (case, tile row << 16 | tile column).
-template <int TX, int TY, int ST, int WALLS>
+template <int TX, int TY, int ST, int WALLS, bool CHK>
 __global__ void __launch_bounds__(TX* TY, (ST == ST_FP32 ? LBM_BATCH_THREADS : LBM_BATCH_THREADS16) /
                                               (TX * TY))
     k_step_batch(const __grid_constant__ BatchTable T, const int2* __restrict__ tiles, int parity,
@@ -1283,11 +1290,11 @@ __global__ void __launch_bounds__(TX* TY, (ST == ST_FP32 ? LBM_BATCH_THREADS : L
     const CaseDesc& cd = T.c[e.x];
     const int c = (cd.cur + parity) & 1;
     if constexpr (ST == ST_FP32) {
-        step_tile<TX, TY, false, WALLS, ST>(sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu,
+        step_tile<TX, TY, false, WALLS, ST, CHK>(sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu,
                                             cd.flag, nullptr, cd.nx, cd.ny, cd.m, (e.y & 0xffff) * TX,
                                             (e.y >> 16) * TY);
     } else {
-        step_tile16<TX, TY, LBM_NPT16_BATCH, WALLS, ST>(
+        step_tile16<TX, TY, LBM_NPT16_BATCH, WALLS, ST, CHK>(
             sphi, cd.f[c], cd.g[c], cd.f[c ^ 1], cd.g[c ^ 1], cd.phiu, cd.flag, cd.nx, cd.ny, cd.m,
             (e.y & 0xffff) * TX, (e.y >> 16) * TY * LBM_NPT16_BATCH);
     }
@@ -1308,26 +1315,29 @@ constexpr int BATCH_TUNE_PER_SHAPE = BATCH_TUNE_WARM + BATCH_TUNE_WINDOW * BATCH
 
 using BatchKernel = void (*)(BatchTable, const int2*, int, int);
 
-template <int ST, int W>
+// the batch kernels test for non-finite nodes when any case asked for checks
+// (CHK), each case then by its own setting
+template <int ST, int W, bool CHK>
 BatchKernel batch_kernel(int cand) {
     switch (cand) {
-        case 0: return k_step_batch<32, 4, ST, W>;
-        case 2: return k_step_batch<32, 16, ST, W>;
-        case 3: return k_step_batch<64, 2, ST, W>;
-        case 4: return k_step_batch<64, 4, ST, W>;
-        default: return k_step_batch<32, 8, ST, W>;
+        case 0: return k_step_batch<32, 4, ST, W, CHK>;
+        case 2: return k_step_batch<32, 16, ST, W, CHK>;
+        case 3: return k_step_batch<64, 2, ST, W, CHK>;
+        case 4: return k_step_batch<64, 4, ST, W, CHK>;
+        default: return k_step_batch<32, 8, ST, W, CHK>;
     }
 }
 
 template <int ST>
-BatchKernel batch_kernel_st(int cls, int cand) {
-    return cls ? batch_kernel<ST, 1>(cand) : batch_kernel<ST, 0>(cand);
+BatchKernel batch_kernel_st(int cls, int cand, bool chk) {
+    if (chk) return cls ? batch_kernel<ST, 1, true>(cand) : batch_kernel<ST, 0, true>(cand);
+    return cls ? batch_kernel<ST, 1, false>(cand) : batch_kernel<ST, 0, false>(cand);
 }
 
-BatchKernel batch_kernel_for(int storage, int cls, int cand) {
-    if (storage == LBM_STORE_FP16_SHIFTED) return batch_kernel_st<ST_FP16>(cls, cand);
-    if (storage == LBM_STORE_BF16_SHIFTED) return batch_kernel_st<ST_BF16>(cls, cand);
-    return batch_kernel_st<ST_FP32>(cls, cand);
+BatchKernel batch_kernel_for(int storage, int cls, int cand, bool chk) {
+    if (storage == LBM_STORE_FP16_SHIFTED) return batch_kernel_st<ST_FP16>(cls, cand, chk);
+    if (storage == LBM_STORE_BF16_SHIFTED) return batch_kernel_st<ST_BF16>(cls, cand, chk);
+    return batch_kernel_st<ST_FP32>(cls, cand, chk);
 }
 
 // Copy the non-finite flags of one class's cases to out[slot[j]] and clear
@@ -1423,7 +1433,7 @@ static void batch_sync_table(lbm_batch* b) {
 
 // one step of class cls with tile shape cand, on the class's stream
 static lbm_status batch_launch(lbm_batch* b, int cls, int cand, int parity) {
-    BatchKernel k = batch_kernel_for(b->storage, cls, cand);
+    BatchKernel k = batch_kernel_for(b->storage, cls, cand, b->check);
     const BatchTable& T = b->tab(cls, cand);
     // programmatic dependent launch, as for the single-case steps (also inside
     // the captured graph, where it becomes a programmatic edge)
