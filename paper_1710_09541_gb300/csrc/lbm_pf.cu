@@ -300,17 +300,22 @@ template <int TX, int TY, int NT, int ST>
 __device__ __forceinline__ void prefetch_tile(const void* fs, const void* gs, const float* phiu,
                                               int nx, int ny, int wfold, int bx, int by) {
     constexpr int NP = Pop<ST>::PLANES;
-    static_assert(NP * (TY + 2) + 2 * TY <= NT, "one request per thread");
+    constexpr int L = (TX + 31) / 32;  // 128-byte lines per tile row of 4-byte entries
+    constexpr int NREQ = (NP * (TY + 2) + 2 * TY) * L;
     const int N = nx * ny;
-    const int t = threadIdx.y * TX + threadIdx.x;
-    const int x0 = bx * TX;
-    if (t < NP * (TY + 2)) {
-        const int plane = t / (TY + 2), r = t - plane * (TY + 2);
-        const int idx = fold_y(by * TY - 1 + r, ny, wfold) * nx + x0;
-        prefetch_l2(Pop<ST>::plane_addr(fs, gs, N, plane, idx));
-    } else if (t < NP * (TY + 2) + 2 * TY) {
-        const int k = t - NP * (TY + 2), yy = by * TY + (k % TY);
-        if (yy < ny) prefetch_l2(phiu + ((k / TY) * N + yy * nx + x0));
+#pragma unroll
+    for (int t0 = threadIdx.y * TX + threadIdx.x; t0 < NREQ; t0 += NT) {
+        const int t = t0 / L, line = t0 - t * L;
+        const int x0 = bx * TX + 32 * line;
+        if (x0 >= nx) continue;
+        if (t < NP * (TY + 2)) {
+            const int plane = t / (TY + 2), r = t - plane * (TY + 2);
+            const int idx = fold_y(by * TY - 1 + r, ny, wfold) * nx + x0;
+            prefetch_l2(Pop<ST>::plane_addr(fs, gs, N, plane, idx));
+        } else {
+            const int k = t - NP * (TY + 2), yy = by * TY + (k % TY);
+            if (yy < ny) prefetch_l2(phiu + ((k / TY) * N + yy * nx + x0));
+        }
     }
 }
 
@@ -322,12 +327,12 @@ __device__ __forceinline__ void prefetch_tile(const void* fs, const void* gs, co
 //   FP32 walls 32.5 / 33.0 k at 8 / 9 (10 spills), 16-bit periodic 49.4 k at 9
 //   against 44.9 k at 10 (with it).
 // LBM_STEP_MINB > 0 overrides all of them.
-template <bool FIELDS, int WALLS, int ST>
+template <bool FIELDS, int WALLS, int ST, int NT>
 constexpr int step_minb() {
     if (LBM_STEP_MINB > 0) return LBM_STEP_MINB;
     if (FIELDS) return 8;
     if (ST == ST_FP32) return WALLS == 0 ? 10 : 9;
-    if (LBM_NPT16 > 1) return 8;  // two nodes per thread: 64 registers, no spills
+    if (LBM_NPT16 > 1) return 1024 / NT;  // two nodes per thread: 64 registers, no spills
     return WALLS == 0 ? 9 : 10;
 }
 
@@ -338,7 +343,7 @@ __host__ __device__ constexpr int step_npt() {
 }
 
 template <int TX, int TY, bool FIELDS, int WALLS, int ST, bool CHK = false>
-__global__ void __launch_bounds__(TX* TY, (step_minb<FIELDS, WALLS, ST>()))
+__global__ void __launch_bounds__(TX* TY, (step_minb<FIELDS, WALLS, ST, TX * TY>()))
     k_step(const float* __restrict__ fs, const float* __restrict__ gs, float* __restrict__ fd,
            float* __restrict__ gd, float* __restrict__ phiu, unsigned int* __restrict__ flag,
            double* __restrict__ out, int nx, int ny, Model m, int pf_ahead) {
@@ -571,6 +576,11 @@ __global__ void __launch_bounds__(RED_THREADS)
 
 // direct-load step: TX x TY threads, one node each (overridable at build time)
 constexpr int STEP_TX = LBM_STEP_TX;
+// thread-block width of the 16-bit steps
+#ifndef LBM_STEP16_TX
+#define LBM_STEP16_TX 32
+#endif
+constexpr int STEP16_TX = LBM_STEP16_TX;
 constexpr int STEP_TY = LBM_STEP_TY;
 constexpr int RED_BLOCKS = 1216;  // 8 x 152 SMs
 }  // namespace
@@ -746,26 +756,28 @@ static cudaError_t launch_dep(void (*k)(Exp...), dim3 grid, dim3 block, cudaStre
 static lbm_status launch_step(lbm_handle* h, bool fields, double* out) {
     const int c = h->cur;
     const bool walls = h->model.walls != 0;
-    dim3 block(STEP_TX, STEP_TY);
     // a 16-bit step's thread takes LBM_NPT16 nodes, so its tile is that many times taller
-    const int th = (!fields && h->prm.storage != LBM_STORE_FP32) ? STEP_TY * LBM_NPT16 : STEP_TY;
-    dim3 grid((h->nx + STEP_TX - 1) / STEP_TX, (h->ny + th - 1) / th);
+    const bool st16 = !fields && h->prm.storage != LBM_STORE_FP32;
+    const int tw = st16 ? STEP16_TX : STEP_TX;
+    const int th = st16 ? STEP_TY * LBM_NPT16 : STEP_TY;
+    dim3 block(tw, STEP_TY);
+    dim3 grid((h->nx + tw - 1) / tw, (h->ny + th - 1) / th);
     using K = void (*)(const float*, const float*, float*, float*, float*, unsigned int*, double*,
                        int, int, Model, int);
     K k;
     // the steps of a handle that asked for non-finite checks test every node;
     // the others are compiled without the test (2% of the 16-bit step)
     const bool chk = h->model.check_nonfinite != 0;
-#define LBM_STEP_KERNEL(ST_)                                                                      \
+#define LBM_STEP_KERNEL(ST_, TW_)                                                                 \
     (fields ? k_step<STEP_TX, STEP_TY, true, -1, ST_>                                            \
-            : (walls ? (chk ? k_step<STEP_TX, STEP_TY, false, 1, ST_, true>                      \
-                            : k_step<STEP_TX, STEP_TY, false, 1, ST_, false>)                    \
-                     : (chk ? k_step<STEP_TX, STEP_TY, false, 0, ST_, true>                      \
-                            : k_step<STEP_TX, STEP_TY, false, 0, ST_, false>)))
+            : (walls ? (chk ? k_step<TW_, STEP_TY, false, 1, ST_, true>                          \
+                            : k_step<TW_, STEP_TY, false, 1, ST_, false>)                        \
+                     : (chk ? k_step<TW_, STEP_TY, false, 0, ST_, true>                          \
+                            : k_step<TW_, STEP_TY, false, 0, ST_, false>)))
     switch (h->prm.storage) {
-        case LBM_STORE_FP16_SHIFTED: k = LBM_STEP_KERNEL(ST_FP16); break;
-        case LBM_STORE_BF16_SHIFTED: k = LBM_STEP_KERNEL(ST_BF16); break;
-        default: k = LBM_STEP_KERNEL(ST_FP32);
+        case LBM_STORE_FP16_SHIFTED: k = LBM_STEP_KERNEL(ST_FP16, STEP16_TX); break;
+        case LBM_STORE_BF16_SHIFTED: k = LBM_STEP_KERNEL(ST_BF16, STEP16_TX); break;
+        default: k = LBM_STEP_KERNEL(ST_FP32, STEP_TX);
     }
 #undef LBM_STEP_KERNEL
     if (fields)
