@@ -24,16 +24,20 @@ using namespace lbmpf;
 namespace {
 
 // ---------------------------------------------------------------------------
-// The fused step kernel.  One thread per node of a TX x TY tile.  Phase 1
-// pulls f_i and g_i of the node, forms phi (Eq. 12) and writes it to shared
-// memory; threads also form phi on the one-node ring around the tile (each
-// ring node pulls its own 9 f_i, mostly L2 hits as neighbouring tiles read
-// the same lines).  Phase 2 takes the stencils of Eqs. 27-28 from shared
-// memory, recovers rho, mu_phi, F, u, p (Eqs. 5-7, 13, 19, 22), collides f and
-// g (Eqs. 8-11, 15-20) and stores both sets at the node's own address.
+// The fused step kernel.  With FP32 storage one thread per node of a TX x TY
+// tile; with 16-bit storage each thread takes LBM_NPT16 nodes of a taller
+// tile (step_tile16).  Phase 1 pulls f_i and g_i of the node, forms phi
+// (Eq. 12) and writes it to shared memory; threads also form phi on the
+// one-node ring around the tile (each ring node pulls its own 9 f_i, mostly
+// L2 hits as neighbouring tiles read the same lines).  Phase 2 takes the
+// stencils of Eqs. 27-28 from shared memory, recovers rho, mu_phi, F, u, p
+// (Eqs. 5-7, 13, 19, 22), collides f and g (Eqs. 8-11, 15-20) and stores both
+// sets at the node's own address.
 //
 // FIELDS = true evaluates the same formulas but writes phi, rho, ux, uy, p
 // as doubles instead of colliding (used by lbm_get_fields and lbm_diag).
+// CHK = true adds the non-finite test of each node (handles that asked for
+// checks).
 // ---------------------------------------------------------------------------
 #ifndef LBM_STEP_TX
 #define LBM_STEP_TX 32
@@ -79,9 +83,9 @@ __device__ __forceinline__ bool nbr_in_range(const Nbr& q, int nx, int ny) {
 #ifndef LBM_PREFETCH16_PER10SM
 #define LBM_PREFETCH16_PER10SM 20
 #endif
-// prefetch with 16-bit storage too (off: those steps are instruction-bound,
-// and the requests cost more than they hide: FP16 at 2048^2 47.6 k -> 45.5 k
-// MLUPS, BF16 47.5 k -> 44.5 k, at their tuned residency)
+// prefetch with 16-bit storage too.  With one node per thread the requests
+// cost more than they hid (FP16 at 2048^2 47.6 k -> 45.5 k MLUPS); with two
+// nodes per thread they pay (54.6 k -> 57.6 k)
 #ifndef LBM_PREFETCH_16
 #define LBM_PREFETCH_16 1
 #endif
@@ -325,7 +329,9 @@ __device__ __forceinline__ void prefetch_tile(const void* fs, const void* gs, co
 //   FP32 periodic 38.7 / 38.6 / 39.4 k; 16-bit periodic 46.5 / 47.6 / 43.6 k;
 //   16-bit walls 41.2 / 42.1 / 42.7 k (before the source-folded collision);
 //   FP32 walls 32.5 / 33.0 k at 8 / 9 (10 spills), 16-bit periodic 49.4 k at 9
-//   against 44.9 k at 10 (with it).
+//   against 44.9 k at 10 (with it).  With two nodes per thread the 16-bit
+//   kernels take 1024 threads per SM (64 registers): 57.6 k at 2048^2, against
+//   56.6 k at 7 blocks (72 registers) and 53.6 k at 10 (spills).
 // LBM_STEP_MINB > 0 overrides all of them.
 template <bool FIELDS, int WALLS, int ST, int NT>
 constexpr int step_minb() {
