@@ -89,9 +89,10 @@ __device__ __forceinline__ bool nbr_in_range(const Nbr& q, int nx, int ny) {
 #ifndef LBM_PREFETCH_16
 #define LBM_PREFETCH_16 1
 #endif
-// also prefetch the tile two distances ahead
-#ifndef LBM_PREFETCH_TWICE
-#define LBM_PREFETCH_TWICE 0
+// alternate the tiles' order from step to step (the step reading buffer 1
+// walks them backwards)
+#ifndef LBM_ALTERNATE_ORDER
+#define LBM_ALTERNATE_ORDER 1
 #endif
 // steps whose algorithmic traffic is below this many tenths of the L2 size
 // run without the prefetch
@@ -352,33 +353,36 @@ template <int TX, int TY, bool FIELDS, int WALLS, int ST, bool CHK = false>
 __global__ void __launch_bounds__(TX* TY, (step_minb<FIELDS, WALLS, ST, TX * TY>()))
     k_step(const float* __restrict__ fs, const float* __restrict__ gs, float* __restrict__ fd,
            float* __restrict__ gd, float* __restrict__ phiu, unsigned int* __restrict__ flag,
-           double* __restrict__ out, int nx, int ny, Model m, int pf_ahead) {
+           double* __restrict__ out, int nx, int ny, Model m, int pf_ahead, int rev) {
     constexpr int NPT = step_npt<FIELDS, ST>();
     __shared__ float sphi[TY * NPT + 2][TX + 2];
+    // rev = 1 walks the tiles in the reverse order (block (0, 0) takes the last
+    // tile): alternate steps meet first the tiles the previous step wrote last,
+    // while they are still in L2
+    const int bx = rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+    const int by = rev ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
     griddep_wait();
     griddep_launch();
     if constexpr (!FIELDS && (ST == ST_FP32 || LBM_PREFETCH_16)) {
         if (pf_ahead > 0) {
             const int lin = blockIdx.y * gridDim.x + blockIdx.x + pf_ahead;
-            if (lin < gridDim.x * gridDim.y)
+            if (lin < gridDim.x * gridDim.y) {
+                int px = lin % gridDim.x, py = lin / gridDim.x;
+                if (rev) {
+                    px = gridDim.x - 1 - px;
+                    py = gridDim.y - 1 - py;
+                }
                 prefetch_tile<TX, TY * NPT, TX * TY, ST>(fs, gs, phiu, nx, ny,
-                                                         WALLS >= 0 ? WALLS : m.walls,
-                                                         lin % gridDim.x, lin / gridDim.x);
-#if LBM_PREFETCH_TWICE
-            const int lin2 = lin + pf_ahead;
-            if (lin2 < gridDim.x * gridDim.y)
-                prefetch_tile<TX, TY * NPT, TX * TY, ST>(fs, gs, phiu, nx, ny,
-                                                         WALLS >= 0 ? WALLS : m.walls,
-                                                         lin2 % gridDim.x, lin2 / gridDim.x);
-#endif
+                                                         WALLS >= 0 ? WALLS : m.walls, px, py);
+            }
         }
     }
     if constexpr (NPT > 1 || (!FIELDS && ST != ST_FP32))
         step_tile16<TX, TY, NPT, WALLS, ST, CHK>(sphi, fs, gs, fd, gd, phiu, flag, nx, ny, m,
-                                            blockIdx.x * TX, blockIdx.y * TY * NPT);
+                                                 bx * TX, by * TY * NPT);
     else
         step_tile<TX, TY, FIELDS, WALLS, ST, CHK>(sphi, fs, gs, fd, gd, phiu, flag, out, nx, ny, m,
-                                             blockIdx.x * TX, blockIdx.y * TY);
+                                                  bx * TX, by * TY);
 }
 
 // ---------------------------------------------------------------------------
@@ -769,7 +773,7 @@ static lbm_status launch_step(lbm_handle* h, bool fields, double* out) {
     dim3 block(tw, STEP_TY);
     dim3 grid((h->nx + tw - 1) / tw, (h->ny + th - 1) / th);
     using K = void (*)(const float*, const float*, float*, float*, float*, unsigned int*, double*,
-                       int, int, Model, int);
+                       int, int, Model, int, int);
     K k;
     // the steps of a handle that asked for non-finite checks test every node;
     // the others are compiled without the test (2% of the 16-bit step)
@@ -788,11 +792,12 @@ static lbm_status launch_step(lbm_handle* h, bool fields, double* out) {
 #undef LBM_STEP_KERNEL
     if (fields)
         k<<<grid, block, 0, h->stream>>>(h->f[c], h->g[c], nullptr, nullptr, h->phiu, h->flag, out,
-                                         h->nx, h->ny, h->model, 0);
+                                         h->nx, h->ny, h->model, 0, 0);
     else
         LBM_CUDA(h, launch_dep(k, grid, block, h->stream, (const float*)h->f[c],
                                (const float*)h->g[c], h->f[c ^ 1], h->g[c ^ 1], h->phiu, h->flag,
-                               (double*)nullptr, h->nx, h->ny, h->model, h->pf_ahead));
+                               (double*)nullptr, h->nx, h->ny, h->model, h->pf_ahead,
+                               LBM_ALTERNATE_ORDER ? c : 0));
     LBM_CUDA(h, cudaGetLastError());
     if (!fields) h->cur ^= 1;
     return LBM_OK;
@@ -1286,16 +1291,19 @@ __global__ void __launch_bounds__(TX* TY, (ST == ST_FP32 ? LBM_BATCH_THREADS : L
     griddep_wait();
     griddep_launch();
     constexpr int TH = TY * (ST == ST_FP32 ? 1 : LBM_NPT16_BATCH);  // tile height in nodes
-    // L2 prefetch of the tile pf_ahead entries later in the list, as in the
+    // odd steps walk the tile list backwards, as the single-case step does
+    const bool rev = LBM_ALTERNATE_ORDER && (parity & 1);
+    const int slot = rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    // L2 prefetch of the tile pf_ahead entries later in the walk, as in the
     // single-case step (0: off)
     if (pf_ahead > 0 && blockIdx.x + pf_ahead < gridDim.x) {
-        const int2 pe = __ldg(tiles + blockIdx.x + pf_ahead);
+        const int2 pe = __ldg(tiles + (rev ? slot - pf_ahead : slot + pf_ahead));
         const CaseDesc& pc = T.c[pe.x < T.ncases ? pe.x : 0];
         const int pcur = (pc.cur + parity) & 1;
         prefetch_tile<TX, TH, TX * TY, ST>(pc.f[pcur], pc.g[pcur], pc.phiu, pc.nx, pc.ny, WALLS,
                                            pe.y & 0xffff, pe.y >> 16);
     }
-    const int2 e = __ldg(tiles + blockIdx.x);
+    const int2 e = __ldg(tiles + slot);
 #if LBM_DEBUG_CHECKS
     if (e.x < 0 || e.x >= T.ncases || (e.y & 0xffff) * TX >= T.c[e.x < 0 || e.x >= T.ncases ? 0 : e.x].nx ||
         (e.y >> 16) * TY * (ST == ST_FP32 ? 1 : LBM_NPT16_BATCH) >=
