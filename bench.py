@@ -255,7 +255,7 @@ def whole_job_mlups(nodes_per_rank, steps, world, seconds):
     return world * nodes_per_rank * steps / seconds / 1e6
 
 
-STORAGE_NAMES = {0: "fp32", 1: "fp16_shifted", 2: "bf16_shifted"}
+STORAGE_NAMES = {0: "fp32", 1: "fp16_shifted", 2: "bf16_shifted", 3: "bf16_shifted_sr"}
 # FP16/BF16 shifted storage: f_0 FP32 (4 B) + f_1..8 and g_0..8 16-bit (34 B)
 # per set, read and written, plus (phi u): 2 * 38 + 16.  The algorithmic
 # minimum of a 16-bit format stores f_0 in 16 bits too: 2 * 36 + 16 = 88 B.
@@ -341,11 +341,12 @@ def run_batched(torch, lbm, stream, steps, storage=1):
 
 
 def run_storage_variants(torch, lbm, stream, steps):
-    """Single-case MLUPS of the 2048 x 2048 workload with 16-bit storage."""
+    """Single-case MLUPS of the 2048 x 2048 workload with 16-bit storage
+    (FP16, BF16, and BF16 with stochastically rounded g codes)."""
     nx, ny = cases.PERF_NX, cases.PERF_NY
     phi0, params = cases.perf_case()
     out = {}
-    for st in (1, 2):
+    for st in (1, 2, 3):
         lat = lbm.Lattice(nx, ny, stream=stream, storage=st, **params).init(phi0)
         lat.step(50)
         t = _time_steps(torch, stream, lambda: lat.step(steps))

@@ -78,7 +78,17 @@ enum {
     LBM_STORE_FP16_SHIFTED = 1, /* f_0 FP32 (takes the rounding of the others, so sum phi is
                                    conserved); f_1..8 FP16 of f_i/w_i - 1/2; g FP16 of
                                    2^10 g_i/w_i (38 B/node) */
-    LBM_STORE_BF16_SHIFTED = 2  /* as FP16_SHIFTED with BF16 and g unscaled */
+    LBM_STORE_BF16_SHIFTED = 2, /* as FP16_SHIFTED with BF16 and g unscaled */
+    LBM_STORE_BF16_SHIFTED_SR = 3 /* the BF16_SHIFTED layout; each step rounds the nine g codes
+                                   stochastically (up with probability equal to the discarded
+                                   fraction, so the stored code is right on average), which keeps
+                                   the slow viscous change of g that rounding to nearest stalls
+                                   at large tau_g.  The dithers come from a counter-based hash of
+                                   the node index and the handle's step count since lbm_init:
+                                   runs are reproducible, and a checkpoint restored into the
+                                   handle that saved it (lbm_set_state keeps the count) resumes
+                                   bit for bit; restored elsewhere it resumes with other dithers.
+                                   Not available in batches (LBM_ERR_INVALID). */
 };
 /* step kernel (kernel) */
 enum {

@@ -51,6 +51,7 @@ struct Model {
                             // ends, 2 bounce-back wall at y = 0 and an open top
     int local_normal;       // Eq. 29 instead of Eq. 2 with Eq. 27
     int check_nonfinite;    // record non-finite nodes in the status flag (check_every > 0)
+    unsigned int seed;      // this step's seed of the stochastic-rounding dithers (BF16_SHIFTED_SR)
 };
 
 // Neighbour addressing of one node: row offsets and wrapped columns.

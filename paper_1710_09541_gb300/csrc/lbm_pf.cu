@@ -284,7 +284,7 @@ __device__ __forceinline__ void step_tile16(float (*sphi)[TX + 2], const void* _
         const float2 now = collide_code<Pop<ST>>(m, h, k, phi, st, M, prev[j]);
         phiu[n[j]] = now.x;
         phiu[N + n[j]] = now.y;
-        Pop<ST>::stfg(fd, gd, N, n[j], h, k, phi);
+        Pop<ST>::stfg(fd, gd, N, n[j], h, k, phi, m.seed);
         if constexpr (CHK)
             if (bad) report_nonfinite(flag);
     }
@@ -617,6 +617,7 @@ struct lbm_handle {
     long long since_check = 0;
     int pf_ahead = 0;  // L2 prefetch distance of the step kernel, in tiles
     bool owns_memory = true;  // false: the device buffers live in a caller's workspace
+    unsigned long long nstep = 0;  // steps since lbm_init: seeds the stochastic rounding
     char err[512] = {0};
 };
 
@@ -660,8 +661,8 @@ static lbm_status validate(int nx, int ny, const lbm_params* p, char* msg, size_
     if (p->normal_scheme != LBM_NORMAL_CENTRAL && p->normal_scheme != LBM_NORMAL_LOCAL)
         return bad("normal_scheme must be 0 or 1");
     if (p->storage != LBM_STORE_FP32 && p->storage != LBM_STORE_FP16_SHIFTED &&
-        p->storage != LBM_STORE_BF16_SHIFTED)
-        return bad("storage must be LBM_STORE_FP32, _FP16_SHIFTED or _BF16_SHIFTED");
+        p->storage != LBM_STORE_BF16_SHIFTED && p->storage != LBM_STORE_BF16_SHIFTED_SR)
+        return bad("storage must be LBM_STORE_FP32, _FP16_SHIFTED, _BF16_SHIFTED or _BF16_SHIFTED_SR");
     if (p->check_every < 0) return bad("check_every must be >= 0");
     if (p->kernel != LBM_KERNEL_AUTO && p->kernel != LBM_KERNEL_GENERIC)
         return bad("kernel must be LBM_KERNEL_AUTO or LBM_KERNEL_GENERIC");
@@ -702,6 +703,12 @@ static void release(lbm_handle* h) {
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, h->stream);
     cudaStreamSynchronize(h->stream);
+}
+
+// BF16_SHIFTED_SR stores the BF16 layout: initialisation, read-back,
+// checkpoints and the impact tools use BF16's kernels
+static bool is_bf16(int storage) {
+    return storage == LBM_STORE_BF16_SHIFTED || storage == LBM_STORE_BF16_SHIFTED_SR;
 }
 
 static size_t f_bytes(int storage, size_t N) {
@@ -787,17 +794,24 @@ static lbm_status launch_step(lbm_handle* h, bool fields, double* out) {
     switch (h->prm.storage) {
         case LBM_STORE_FP16_SHIFTED: k = LBM_STEP_KERNEL(ST_FP16, STEP16_TX); break;
         case LBM_STORE_BF16_SHIFTED: k = LBM_STEP_KERNEL(ST_BF16, STEP16_TX); break;
+        // the read-back of the stochastically rounded format is BF16's
+        case LBM_STORE_BF16_SHIFTED_SR:
+            k = fields ? LBM_STEP_KERNEL(ST_BF16, STEP16_TX) : LBM_STEP_KERNEL(ST_BF16_SR, STEP16_TX);
+            break;
         default: k = LBM_STEP_KERNEL(ST_FP32, STEP_TX);
     }
 #undef LBM_STEP_KERNEL
     if (fields)
         k<<<grid, block, 0, h->stream>>>(h->f[c], h->g[c], nullptr, nullptr, h->phiu, h->flag, out,
                                          h->nx, h->ny, h->model, 0, 0);
-    else
+    else {
+        // a distinct seed per step (the golden-ratio multiple of the step count)
+        h->model.seed = (unsigned int)(++h->nstep) * 0x9e3779b9u;
         LBM_CUDA(h, launch_dep(k, grid, block, h->stream, (const float*)h->f[c],
                                (const float*)h->g[c], h->f[c ^ 1], h->g[c ^ 1], h->phiu, h->flag,
                                (double*)nullptr, h->nx, h->ny, h->model, h->pf_ahead,
                                LBM_ALTERNATE_ORDER ? c : 0));
+    }
     LBM_CUDA(h, cudaGetLastError());
     if (!fields) h->cur ^= 1;
     return LBM_OK;
@@ -953,15 +967,16 @@ lbm_status lbm_init(lbm_handle* h, const double* phi0, const double* ux0, const 
             LBM_CUDA(h, cudaMemsetAsync(in + k * h->N, 0, bytes, h->stream));
     }
     h->cur = 0;
-    auto kinit = h->prm.storage == LBM_STORE_FP16_SHIFTED   ? k_init<ST_FP16>
-                 : h->prm.storage == LBM_STORE_BF16_SHIFTED ? k_init<ST_BF16>
-                                                            : k_init<ST_FP32>;
+    auto kinit = h->prm.storage == LBM_STORE_FP16_SHIFTED ? k_init<ST_FP16>
+                 : is_bf16(h->prm.storage)                ? k_init<ST_BF16>
+                                                          : k_init<ST_FP32>;
     kinit<<<grid1d(h->N), 256, 0, h->stream>>>(in, h->f[0], h->g[0], h->phiu, h->nx, h->ny,
                                                  h->model);
     LBM_CUDA(h, cudaGetLastError());
     LBM_CUDA(h, cudaMemsetAsync(h->flag, 0, sizeof(unsigned int), h->stream));
     LBM_CUDA(h, cudaStreamSynchronize(h->stream));
     h->inited = true;
+    h->nstep = 0;
     h->since_check = 0;
     return LBM_OK;
 }
@@ -1007,9 +1022,9 @@ lbm_status lbm_get_state(lbm_handle* h, void* host_buf, size_t bytes) {
     if (!h->inited) return fail(h, LBM_ERR_STATE, "lbm_get_state before lbm_init");
     LBM_CUDA(h, cudaSetDevice(h->device));
     float* st = (float*)h->staging;
-    auto kout = h->prm.storage == LBM_STORE_FP16_SHIFTED   ? k_state_out<ST_FP16>
-                : h->prm.storage == LBM_STORE_BF16_SHIFTED ? k_state_out<ST_BF16>
-                                                           : k_state_out<ST_FP32>;
+    auto kout = h->prm.storage == LBM_STORE_FP16_SHIFTED ? k_state_out<ST_FP16>
+                : is_bf16(h->prm.storage)                ? k_state_out<ST_BF16>
+                                                          : k_state_out<ST_FP32>;
     kout<<<grid1d(h->N), 256, 0, h->stream>>>(h->f[h->cur], h->g[h->cur], h->phiu, st,
                                                       h->nx, h->ny, h->model.walls);
     LBM_CUDA(h, cudaGetLastError());
@@ -1027,9 +1042,9 @@ lbm_status lbm_set_state(lbm_handle* h, const void* host_buf, size_t bytes) {
     float* st = (float*)h->staging;
     LBM_CUDA(h, cudaMemcpyAsync(st, host_buf, bytes, cudaMemcpyHostToDevice, h->stream));
     h->cur = 0;
-    auto kin = h->prm.storage == LBM_STORE_FP16_SHIFTED   ? k_state_in<ST_FP16>
-               : h->prm.storage == LBM_STORE_BF16_SHIFTED ? k_state_in<ST_BF16>
-                                                          : k_state_in<ST_FP32>;
+    auto kin = h->prm.storage == LBM_STORE_FP16_SHIFTED ? k_state_in<ST_FP16>
+               : is_bf16(h->prm.storage)                ? k_state_in<ST_BF16>
+                                                         : k_state_in<ST_FP32>;
     kin<<<grid1d(h->N), 256, 0, h->stream>>>(st, h->f[0], h->g[0], h->phiu, h->nx,
                                                      h->ny, h->model.walls);
     LBM_CUDA(h, cudaGetLastError());
@@ -1594,6 +1609,13 @@ lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** ou
                 return LBM_ERR_INVALID;
             }
     }
+    // the graph replays fixed launches, so it has no per-step seed to give
+    // the dithers of stochastic rounding
+    if (cases[0]->prm.storage == LBM_STORE_BF16_SHIFTED_SR) {
+        fprintf(stderr, "lbm_batch_create: LBM_STORE_BF16_SHIFTED_SR is not available in batches "
+                        "(step such cases one by one)\n");
+        return LBM_ERR_INVALID;
+    }
     lbm_batch* b = new (std::nothrow) lbm_batch();
     if (!b) return LBM_ERR_OOM;
     b->ncases = ncases;
@@ -2004,9 +2026,9 @@ lbm_status lbm_spreading_radius(lbm_handle* h, int y, int xc, double* r, double*
         return fail(h, LBM_ERR_INVALID, "lbm_spreading_radius: (xc, y) = (%d, %d) outside the grid",
                     xc, y);
     LBM_CUDA(h, cudaSetDevice(h->device));
-    auto k = h->prm.storage == LBM_STORE_FP16_SHIFTED   ? k_spreading_radius<ST_FP16>
-             : h->prm.storage == LBM_STORE_BF16_SHIFTED ? k_spreading_radius<ST_BF16>
-                                                        : k_spreading_radius<ST_FP32>;
+    auto k = h->prm.storage == LBM_STORE_FP16_SHIFTED ? k_spreading_radius<ST_FP16>
+             : is_bf16(h->prm.storage)                ? k_spreading_radius<ST_BF16>
+                                                       : k_spreading_radius<ST_FP32>;
     k<<<1, 1024, 0, h->stream>>>(h->f[h->cur], h->nx, h->ny, h->model.walls, y, xc, h->red_res);
     LBM_CUDA(h, cudaGetLastError());
     double res[4];
@@ -2039,9 +2061,9 @@ lbm_status lbm_probe(lbm_handle* h, int npts, const int* x, const int* y, double
     double* d_out = (double*)h->staging + h->N;
     LBM_CUDA(h, cudaMemcpyAsync(d_xy, xy.data(), xy.size() * sizeof(int), cudaMemcpyHostToDevice,
                                 h->stream));
-    auto k = h->prm.storage == LBM_STORE_FP16_SHIFTED   ? k_probe<ST_FP16>
-             : h->prm.storage == LBM_STORE_BF16_SHIFTED ? k_probe<ST_BF16>
-                                                        : k_probe<ST_FP32>;
+    auto k = h->prm.storage == LBM_STORE_FP16_SHIFTED ? k_probe<ST_FP16>
+             : is_bf16(h->prm.storage)                ? k_probe<ST_BF16>
+                                                       : k_probe<ST_FP32>;
     const int blocks = (npts + 127) / 128 < 1184 ? (npts + 127) / 128 : 1184;
     k<<<blocks, 128, 0, h->stream>>>(h->f[h->cur], h->g[h->cur], h->nx, h->ny, h->model, d_xy,
                                       npts, d_out);

@@ -24,6 +24,10 @@
 //   the g_0 codes (N 16-bit values).
 //   Bytes per node: 4 + 32 + 2 = 38 per set (92 B read + written per update
 //   with phi u).
+//
+//   BF16 shifted with stochastic rounding (LBM_STORE_BF16_SHIFTED_SR): the
+//   BF16 layout; the step rounds the nine g codes stochastically (the f codes
+//   and the read-back, initialisation and checkpoints as BF16_SHIFTED).
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -44,7 +48,7 @@
 
 namespace lbmpf {
 
-enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2 };
+enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2, ST_BF16_SR = 3 };
 
 template <int ST>
 struct Pop;
@@ -59,7 +63,7 @@ struct Pop<ST_FP32> {
     // rounding of the collision.  Stores of f_i and g_i interleaved (as
     // measured fastest).
     __device__ static void stfg(void* fb, void* gb, int N, int idx, const float f[9],
-                                const float g[9], float phi) {
+                                const float g[9], float phi, unsigned int = 0) {
         float* F = static_cast<float*>(fb);
         float* G = static_cast<float*>(gb);
 #if LBM_STORE_STREAMING
@@ -133,13 +137,50 @@ struct Half16<__nv_bfloat16> {
     }
 };
 
+// Stochastic rounding of the g codes (LBM_STORE_BF16_SHIFTED_SR).  BF16 keeps
+// 8 significant bits, and where tau_g is large (low Reynolds numbers) the
+// change a collision makes to a g code each step is a small fraction of its
+// spacing: rounding to nearest then returns the same code step after step and
+// the slow viscous evolution stalls.  Rounding up with probability equal to
+// the discarded fraction makes the stored code right on average, E[code] = v.
+//
+// The uniform 16-bit dithers come from a counter-based hash of (node, step):
+// a 32-bit base per node, lowbias32 (C. Wellons, "Prospecting for hash
+// functions", 2018: x ^= x >> 16; x *= 0x7feb352d; x ^= x >> 15;
+// x *= 0x846ca68b; x ^= x >> 16) of the node index xor the step seed, then
+// for j = 0..4 the product (base + j * 0x9e3779b9) * 0x85ebca6b, whose upper
+// and lower halves serve directions 2j + 1 and 2j + 2 (j < 4) and the rest
+// direction (the upper half of j = 4).  For a fixed node and
+// direction each half is uniform, and independent from step to step through
+// the seed; the dithers of one node's directions are correlated, which leaves
+// each direction's rounding unbiased.
+__device__ __forceinline__ unsigned int lowbias32(unsigned int x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+// v rounded to BF16 (its upper 16 bits) with the dither r in [0, 2^16):
+// adding r to the discarded half carries into the kept half with probability
+// (discarded half) / 2^16.  Inf and NaN are truncated without dither, so they
+// stay Inf and NaN (a dither could carry a NaN's all-ones pattern into the
+// sign bit).
+__device__ __forceinline__ unsigned int bf16_sr_bits(float v, unsigned int r) {
+    const unsigned int b = __float_as_uint(v);
+    const unsigned int d = (b & 0x7fffffffu) < 0x7f800000u ? r : 0u;
+    return (b + d) >> 16;
+}
+
 // The 16-bit formats store codes: h_i = f_i / w_i - 1/2 for the moving f_i
 // and k_i = GS g_i / w_i for every g_i.  The step reads them as codes (one
 // conversion each, no scaling), forms phi and the moments of g with the
 // weights factored out per weight class, collides in code units
 // (collide_code) and writes the new codes with one packed conversion per
 // direction: decode and encode cost no arithmetic.  f_0 stays an FP32 value.
-template <typename H>
+// SR (BF16 only): the step's stores round the g codes stochastically.
+template <typename H, bool SR = false>
 struct Shifted16 {
     using C = Half16<H>;
     static constexpr float GS = C::GS;
@@ -204,19 +245,35 @@ struct Shifted16 {
         return sub(phi, s8(h));
     }
     // store the post-collision codes of node idx: h_i | k_i << 16 per moving
-    // direction, k_0, and f_0 as the remainder phi - s8(stored codes)
+    // direction, k_0, and f_0 as the remainder phi - s8(stored codes); seed
+    // (SR only) is the step's seed of the dithers
     __device__ static void stfg(void* fb, void* gb, int N, int idx, const float h[9],
-                                const float k[9], float phi) {
+                                const float k[9], float phi, unsigned int seed = 0) {
+        static_assert(!SR || C::GS == 1.f, "stochastic rounding is a BF16 format");
         unsigned int* P = pw(fb, N);
         float d[9];
+        unsigned int base = 0, r = 0;
+        if constexpr (SR) base = lowbias32((unsigned int)idx ^ seed);
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            const unsigned int w = C::pack(h[i], k[i]);
+            unsigned int w;
+            if constexpr (SR) {
+                // directions 2j - 1 and 2j take the halves of product j
+                if (i & 1) r = (base + (unsigned int)(i >> 1) * 0x9e3779b9u) * 0x85ebca6bu;
+                const unsigned int ri = (i & 1) ? (r >> 16) : (r & 0xffffu);
+                w = (unsigned int)C::from_f(h[i]) | (bf16_sr_bits(k[i], ri) << 16);
+            } else {
+                w = C::pack(h[i], k[i]);
+            }
             P[(i - 1) * N + idx] = w;
             d[i] = C::to_f(lo(w));
         }
         static_cast<float*>(fb)[idx] = sub(phi, s8(d));
-        static_cast<unsigned short*>(gb)[idx] = C::from_f(k[0]);
+        if constexpr (SR)
+            static_cast<unsigned short*>(gb)[idx] =
+                (unsigned short)bf16_sr_bits(k[0], ((base + 4u * 0x9e3779b9u) * 0x85ebca6bu) >> 16);
+        else
+            static_cast<unsigned short*>(gb)[idx] = C::from_f(k[0]);
     }
     // one entry (checkpoint and initial-state permutations)
     __device__ static void putf(void* fb, int N, int i, int idx, float v) {
@@ -246,6 +303,8 @@ template <>
 struct Pop<ST_FP16> : Shifted16<__half> {};
 template <>
 struct Pop<ST_BF16> : Shifted16<__nv_bfloat16> {};
+template <>
+struct Pop<ST_BF16_SR> : Shifted16<__nv_bfloat16, true> {};
 
 // Both collisions of one node in the code units of a 16-bit format (the
 // same update as collide, Eqs. 2, 3, 8, 9, 11 and 15-17, 20, divided through

@@ -25,7 +25,7 @@ _STATUS = {0: "LBM_OK", -1: "LBM_ERR_INVALID", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_
 LBM_VISC_LINEAR_NU, LBM_VISC_INVERSE_NU, LBM_VISC_STEP_MU = 0, 1, 2
 LBM_BC_PERIODIC, LBM_BC_WALLS, LBM_BC_WALL_OPEN = 0, 1, 2
 LBM_NORMAL_CENTRAL, LBM_NORMAL_LOCAL = 0, 1
-LBM_STORE_FP32, LBM_STORE_FP16_SHIFTED, LBM_STORE_BF16_SHIFTED = 0, 1, 2
+LBM_STORE_FP32, LBM_STORE_FP16_SHIFTED, LBM_STORE_BF16_SHIFTED, LBM_STORE_BF16_SHIFTED_SR = 0, 1, 2, 3
 LBM_KERNEL_AUTO, LBM_KERNEL_GENERIC = 0, 1
 
 # every entry point include/lbm_pf.h declares

@@ -102,6 +102,22 @@ def test_workspace_bytes_and_create_in_checks(L):
     assert not h.value
 
 
+def test_storage_formats_and_their_sizes(L):
+    """The stochastically rounded BF16 format keeps BF16's layout; an unknown
+    format is rejected."""
+    sizes = []
+    for st in (lbm.LBM_STORE_FP16_SHIFTED, lbm.LBM_STORE_BF16_SHIFTED, lbm.LBM_STORE_BF16_SHIFTED_SR):
+        p = lbm.make_params(storage=st)
+        n = ctypes.c_size_t()
+        assert L.lbm_workspace_bytes(64, 32, ctypes.byref(p), ctypes.byref(n)) == lbm.LBM_OK
+        sizes.append(n.value)
+    assert sizes[0] == sizes[1] == sizes[2]
+    n = ctypes.c_size_t()
+    for st in (-1, 4):
+        p = lbm.make_params(storage=st)
+        assert L.lbm_workspace_bytes(64, 32, ctypes.byref(p), ctypes.byref(n)) == lbm.LBM_ERR_INVALID
+
+
 def test_open_top_needs_two_rows(L):
     p = lbm.make_params(bc_y=lbm.LBM_BC_WALL_OPEN)
     h = ctypes.c_void_p()
@@ -113,7 +129,8 @@ def test_header_enum_values_match_the_binding():
     import re
     text = open(os.path.join(ROOT, "include", "lbm_pf.h")).read()
     for name in ("LBM_BC_PERIODIC", "LBM_BC_WALLS", "LBM_BC_WALL_OPEN", "LBM_STORE_FP32",
-                 "LBM_STORE_FP16_SHIFTED", "LBM_STORE_BF16_SHIFTED", "LBM_KERNEL_AUTO",
+                 "LBM_STORE_FP16_SHIFTED", "LBM_STORE_BF16_SHIFTED", "LBM_STORE_BF16_SHIFTED_SR",
+                 "LBM_KERNEL_AUTO",
                  "LBM_KERNEL_GENERIC"):
         m = re.search(name + r"\s*=\s*(\d+)", text)
         assert m and int(m.group(1)) == getattr(lbm, name), name

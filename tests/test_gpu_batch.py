@@ -105,6 +105,19 @@ def test_batch_rejects_mixed_storage_and_repeats(lbm):
         b.close()
 
 
+def test_batch_rejects_stochastic_rounding(lbm):
+    """A batch replays fixed launches, which have no per-step seed for the
+    dithers: BF16_SHIFTED_SR cases are stepped one by one."""
+    specs = cases.batch_cases(n=2, seed=3)
+    lats = _lattices(lbm, specs, 3)
+    try:
+        with pytest.raises(lbm.LbmError):
+            lbm.Batch(lats)
+    finally:
+        for lat in lats:
+            lat.close()
+
+
 def test_batch_at_the_case_limit(lbm):
     """200 small cases (the kernel-parameter table's capacity) of mixed
     boundary kinds and sizes; a 201st is rejected."""

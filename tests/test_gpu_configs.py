@@ -26,6 +26,12 @@ holds the 16-bit run to what such round-off-level perturbations do:
   FP16-shifted storage stays within 0.63% of FP32 at every sample for all
   three Reynolds numbers (bound 2%): its 11 significant bits resolve the
   per-step viscous change of the g codes that BF16's 8 bits round away.
+  BF16 with the g codes rounded stochastically (BF16_SHIFTED_SR) keeps that
+  change on average: at Re = 20 it stays within 0.6% of FP32 at every sample
+  (four runs).  At Re = 100 and 500 the rounding noise decides when the lamella
+  pinches off: in one of four Re = 100 runs a pinch-off at t* = 0.5 (+17.5%)
+  left the radius 8-10% behind FP32 to t* = 4; the other three ended within
+  2.9%.  At Re = 500 the final radius agreed within 0.3%.
   The power law r/D = C sqrt(t*) of Sec. III D (C = 1.35 at its own U = 0.05)
   holds with C in [0.9, 1.5] once the lamella has formed."""
 import numpy as np
@@ -91,12 +97,12 @@ def test_spinodal_1024_fp32_vs_fp16(lbm, ratio):
 
 
 @pytest.mark.parametrize("Re", [20.0, 100.0, 500.0])
-def test_impact_2400x600_fp32_vs_bf16(lbm, Re):
+def test_impact_2400x600_fp32_vs_16bit(lbm, Re):
     P = cases.params_impact(Re=Re)
     phi0, u0, v0 = cases.impact(2400, 600, 200.0, 20.0, 0.04, P["W"])
     row = int(round(20 + P["W"]))
     radii = {}
-    for st, k in ((0, 0), (0, 1), (2, 0), (1, 0)):
+    for st, k in ((0, 0), (0, 1), (2, 0), (1, 0), (3, 0)):
         with lbm.Lattice(2400, 600, storage=st, **P) as g:
             g.init(_perturbed(phi0, k), u0, v0)
             r = []
@@ -112,10 +118,15 @@ def test_impact_2400x600_fp32_vs_bf16(lbm, Re):
     # at Re = 20, 100 and 500), the target config 4 sets for the radius
     assert np.all(np.abs(radii[1, 0] / r32 - 1) < 0.02), (r32, radii[1, 0])
     dev = np.abs(radii[2, 0] / r32 - 1)
+    dsr = np.abs(radii[3, 0] / r32 - 1)
     if Re == 20.0:
         assert np.all(dev < 0.15) and dev[-1] < 0.12, (r32, radii[2, 0])
+        # stochastic rounding removes the deposition's bias (measured 0.6%)
+        assert np.all(dsr < 0.015), (r32, radii[3, 0])
     else:
         assert np.all(dev < 0.25) and dev[-1] < 0.03, (r32, radii[2, 0])
+        # the noise can move a pinch-off, after which the radius trails (8.6% measured)
+        assert np.all(dsr < 0.25) and dsr[-1] < 0.15, (r32, radii[3, 0])
         t = np.arange(1, 9) * 0.5
         C = r32 / 200.0 / np.sqrt(t)
         assert np.all((C[1:] > 0.9) & (C[1:] < 1.5)), C

@@ -1,12 +1,17 @@
-"""Shifted 16-bit population storage (LBM_STORE_FP16_SHIFTED, _BF16_SHIFTED):
-arithmetic stays FP32, only the stored populations are rounded.
+"""Shifted 16-bit population storage (LBM_STORE_FP16_SHIFTED, _BF16_SHIFTED,
+_BF16_SHIFTED_SR): arithmetic stays FP32, only the stored populations are
+rounded.
 
 * One step from an identical, representable state: every population within
   the rounding the format allows, plus the FP32 and n-conditioning terms of
   the FP32 parity tests.  A moving f_i stores v = f_i/w_i - 1/2 with a 16-bit
   significand (p = 11 for FP16, 8 for BF16), so it may differ by
   w_i 2^-p |v|; the rest population f_0 absorbs the rounding of the eight
-  others; g_i stores S g_i / w_i and may differ by 2^-p of itself.
+  others; g_i stores S g_i / w_i and may differ by 2^-p of itself (2^(1-p),
+  one spacing, when rounded stochastically).
+* Stochastic rounding is unbiased: over 64 steps from one state, each with
+  its own dithers, the mean stored g_i converges on the unrounded value (the
+  same step with FP32 storage), and the f codes are those of BF16_SHIFTED.
 * sum phi stays conserved (f_0 is the remainder of the node's phi).
 * A saved state restores bit for bit.
 * Accuracy on the 64 x 64 static droplet (R = 16, ratio 1000) against the FP64 oracle: the
@@ -23,7 +28,8 @@ from paper_1710_09541_gb300 import cases
 pytestmark = pytest.mark.gpu
 
 W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
-FORMATS = {1: (2.0 ** -11, 1024.0), 2: (2.0 ** -8, 1.0)}   # storage -> (half ulp, g scale)
+# storage -> (half spacing 2^-p, g scale S, bound on the g rounding in half spacings)
+FORMATS = {1: (2.0 ** -11, 1024.0, 1.0), 2: (2.0 ** -8, 1.0, 1.0), 3: (2.0 ** -8, 1.0, 2.0)}
 
 
 @pytest.fixture(scope="module")
@@ -62,12 +68,12 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("storage", [1, 2, 3])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_one_step_within_format_rounding(lbm, storage, name):
     nx, ny, P, init, t0 = CASES[name]
     walls = P.get("bc_y", 0) == 1
-    u, S = FORMATS[storage]
+    u, S, gr = FORMATS[storage]
     st = oracle.Lattice(nx, ny, **P).init(init()).step(t0).get_state()
     with lbm.Lattice(nx, ny, storage=storage, **P) as g:
         g.set_state(*(a.astype(np.float32) for a in st))
@@ -89,12 +95,12 @@ def test_one_step_within_format_rounding(lbm, storage, name):
     bf = W * (1.01 * u * v + 2.0 ** -24) + fp32
     bf[0] = fp32[0] + bf[1:].sum(axis=0)
     assert np.all(np.abs(gf - of) <= bf), float((np.abs(gf - of) / bf).max())
-    bg = W / S * (1.01 * u * np.abs(og) * S / W + 2.0 ** -24) + 5e-6 * np.abs(og).max()
+    bg = W / S * (1.01 * gr * u * np.abs(og) * S / W + 2.0 ** -24) + 5e-6 * np.abs(og).max()
     assert np.all(np.abs(gg - og) <= bg), float((np.abs(gg - og) / bg).max())
     assert np.abs(gu - ou).max() <= 5e-6 * np.abs(ou).max() + 1e-8   # phi u is stored in FP32
 
 
-@pytest.mark.parametrize("storage", [0, 1, 2])
+@pytest.mark.parametrize("storage", [0, 1, 2, 3])
 def test_sum_phi_conserved(lbm, storage):
     """The rest population is written as the remainder of the node's phi, so
     sum phi moves only by FP32 round-off (FP64 accumulation of the diagnostic)."""
@@ -113,10 +119,10 @@ def test_sum_phi_conserved(lbm, storage):
 # measured over 1000 steps on the first twelve drops and impacts of the
 # batched sweep: worst |drift| FP32 2.9e-7, FP16 4.3e-7, BF16 1.3e-6 (before
 # phi and the remainder shared one association order, FP16 drifted 1.4e-5)
-DRIFT_1000 = {0: 1e-6, 1: 1.5e-6, 2: 4e-6}
+DRIFT_1000 = {0: 1e-6, 1: 1.5e-6, 2: 4e-6, 3: 4e-6}
 
 
-@pytest.mark.parametrize("storage", [0, 1, 2])
+@pytest.mark.parametrize("storage", [0, 1, 2, 3])
 def test_sum_phi_drop_in_gas(lbm, storage):
     """A drop in a large gas region (576 x 448, ratio 10): bulk liquid with
     16-bit populations, where a rounding bias would show as a steady loss."""
@@ -130,8 +136,11 @@ def test_sum_phi_drop_in_gas(lbm, storage):
     assert abs(s1 / s0 - 1) < DRIFT_1000[storage], s1 / s0 - 1
 
 
-@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("storage", [1, 2, 3])
 def test_checkpoint_resume_bit_exact(lbm, storage):
+    """A saved state restored into the handle that saved it resumes bit for
+    bit (with stochastic rounding: the handle's step count, which seeds the
+    dithers, is not part of the checkpoint and carries on)."""
     nx, ny = 70, 50
     P = cases.params_static_drop()
     phi0 = cases.drop(nx, ny, 12, 4.0)
@@ -145,11 +154,13 @@ def test_checkpoint_resume_bit_exact(lbm, storage):
 
 # measured on GB300 after 3000 steps (oracle: max|u| 8.26e-5, dp 8.09e-4):
 # FP32 8.6e-5 / 7.93e-4, FP16-shifted 9.2e-5 / 8.10e-4, BF16-shifted 3.2e-4 / 8.94e-4;
-# time-averaged jump against the oracle: FP32 and FP16 within 1%, BF16 21% high
-ACCURACY = {0: (0.03, 1.2), 1: (0.03, 1.5), 2: (0.30, 6.0)}   # storage -> (dp rel, umax factor)
+# time-averaged jump against the oracle: FP32 and FP16 within 1%, BF16 21% high;
+# BF16 with stochastic rounding: jump 6.4% low, max|u| 4.6e-4 (3.3x the oracle's over the
+# 16 samples against 2.7x for BF16: less bias, more noise)
+ACCURACY = {0: (0.03, 1.2), 1: (0.03, 1.5), 2: (0.30, 6.0), 3: (0.30, 6.0)}   # storage -> (dp rel, umax factor)
 
 
-@pytest.mark.parametrize("storage", [0, 1, 2])
+@pytest.mark.parametrize("storage", [0, 1, 2, 3])
 def test_static_drop_accuracy_per_storage(lbm, storage):
     """Static drop (64 x 64, R = 16, ratio 1000, sigma = 0.01): time-averaged
     Laplace jump and spurious-velocity maximum against the FP64 oracle."""
@@ -217,17 +228,78 @@ def planar_at_rest(lat_cls, ny, steps=10000, **kw):
 # roundings of the same collision put the BF16 jump at 4.6e-8 and at 2.7e-7 (the
 # latter with the g equilibria of opposite directions formed as A + B and A - B),
 # so BF16 is held to about three times its resolution.
-PLANAR_JUMP = {0: 1e-7, 1: 2.5e-7, 2: 1e-6}
+PLANAR_JUMP = {0: 1e-7, 1: 2.5e-7, 2: 1e-6, 3: 1e-6}
+# Stochastic rounding trades the g codes' bias for noise of about one spacing per
+# step; in the gas (rho_g = 1e-3) that noise divided by rho is a velocity of
+# order 1e-5 (measured 2.1e-5 / 2.3e-6 at ny = 64 / 63, jump 7.2e-8 / 6.9e-8).
+PLANAR_SPEED = {0: 1e-6, 1: 1e-6, 2: 1e-6, 3: 1e-4}
 
 
 @pytest.mark.parametrize("ny", [64, 63])
-@pytest.mark.parametrize("storage", [0, 1, 2])
+@pytest.mark.parametrize("storage", [0, 1, 2, 3])
 def test_planar_interface_at_rest_per_storage(lbm, storage, ny):
     """A flat interface has no curvature, hence no jump and no flow (the
     Laplace law at R -> inf).  After 1e4 steps the phi = 1/2 crossing has
     moved by less than 1e-3 node, and over the next 1e4 steps by less than
     1e-5; the jump stays below PLANAR_JUMP (sigma / W = 2.5e-4), phi within
-    1e-2 of Eq. 33's tanh, the speed below 1e-6."""
+    1e-2 of Eq. 33's tanh, the speed below PLANAR_SPEED (1e-6 but for the
+    stochastically rounded format)."""
     dh, drift, jump, dphi, speed = planar_at_rest(lbm.Lattice, ny, storage=storage)
     assert abs(dh) < 1e-3 and abs(drift) < 1e-5, (dh, drift)
-    assert abs(jump) < PLANAR_JUMP[storage] and dphi < 1e-2 and speed < 1e-6, (jump, dphi, speed)
+    assert abs(jump) < PLANAR_JUMP[storage] and dphi < 1e-2, (jump, dphi)
+    assert speed < PLANAR_SPEED[storage], speed
+
+
+def _bf16_spacing(v):
+    """Spacing of the BF16 values around |v| (8 significant bits; normal range)."""
+    e = np.floor(np.log2(np.maximum(np.abs(v), 2.0 ** -126)))
+    return 2.0 ** (e - 7)
+
+
+SR_SAMPLES = 64
+
+
+@pytest.mark.parametrize("name", ["spinodal", "static_drop"])
+def test_bf16_sr_unbiased(lbm, name):
+    """One step from one representable state, taken SR_SAMPLES times with
+    BF16_SHIFTED_SR (each step of the handle has its own dithers): every
+    stored g code lies within one BF16 spacing of the unrounded value (the
+    same step with FP32 storage), the samples differ, and their mean
+    converges on it (per element the mean's error is p(1 - p) / K in
+    variance, RMS sqrt(1/(6K)) = 0.051 spacings for a uniform fraction p;
+    rounding to nearest would leave a fixed error of RMS 0.29).  The f codes
+    and (phi u) are BF16_SHIFTED's, bit for bit."""
+    nx, ny, P, init, t0 = CASES[name]
+    st = oracle.Lattice(nx, ny, **P).init(init()).step(t0).get_state()
+    with lbm.Lattice(nx, ny, storage=3, **P) as g, lbm.Lattice(nx, ny, storage=0, **P) as e, \
+            lbm.Lattice(nx, ny, storage=2, **P) as rn:
+        g.set_state(*(a.astype(np.float32) for a in st))
+        rep = g.get_state()
+        e.set_state(*rep)
+        e.step(1)
+        ge = e.get_state()[1].astype(np.float64)
+        rn.set_state(*rep)
+        rn.step(1)
+        rf, rg, ru = rn.get_state()
+        samples = []
+        for _ in range(SR_SAMPLES):
+            g.set_state(*rep)
+            g.step(1)
+            sf, sg, su = g.get_state()
+            assert np.array_equal(sf, rf) and np.array_equal(su, ru)
+            samples.append(sg.astype(np.float64))
+    s = np.array(samples)
+    spacing = W * _bf16_spacing(ge / W)                      # one BF16 step of g_i in population units
+    floor = 5e-6 * np.abs(ge).max()                          # FP32 part (two arithmetic orders)
+    err = np.abs(s - ge[None])
+    assert np.all(err <= 1.001 * spacing[None] + floor), float((err / (spacing + floor)).max())
+    well = spacing > 100 * floor                             # elements where the rounding dominates
+    assert well.sum() > 2000, well.sum()                     # spinodal 59 189, static drop 4 889
+    m = (s.mean(axis=0) - ge)[well] / spacing[well]
+    rms = float(np.sqrt(np.mean(m ** 2)))
+    assert rms < 0.08, rms
+    varies = (s.std(axis=0)[well] > 0).mean()
+    assert varies > 0.5, varies
+    mrn = (rg.astype(np.float64) - ge)[well] / spacing[well]
+    print(f"{name}: SR mean error RMS {rms:.4f} spacings over {well.sum()} values "
+          f"(rounding to nearest: {np.sqrt(np.mean(mrn ** 2)):.4f}), varying {varies:.3f}")
