@@ -249,7 +249,7 @@ lbm_status lbm_diag_fields_noalloc(const double* d_fields, size_t n, double* d_o
  *
  * lbm_batch_create -- build the batch over ncases handles (1 <= ncases <= 200,
  *   each initialised, none repeated, each with at most 65535 x 32767 tiles of
- *   the smallest tile shape).  The batch owns a case table, device tile
+ *   the smallest tile shape, none with LBM_STORE_BF16_SHIFTED_SR storage).  The batch owns a case table, device tile
  *   lists (8 bytes per tile per tile shape and class) and two private
  *   streams; handles must outlive the batch.
  *   Errors: LBM_ERR_INVALID, LBM_ERR_OOM, LBM_ERR_CUDA (then *out == NULL).
