@@ -95,9 +95,19 @@ __device__ __forceinline__ bool nbr_in_range(const Nbr& q, int nx, int ny) {
 #define LBM_ALTERNATE_ORDER 1
 #endif
 // steps whose algorithmic traffic is below this many tenths of the L2 size
-// run without the prefetch
+// run without the prefetch: FP32 and 16-bit storage.  With the alternating
+// tile order, measured with one grid per process (MLUPS, prefetch on / off):
+// FP32 1024^2 (168 MB per step) 38.6 / 39.6 k, FP32 impact 2400 x 600
+// (230 MB) 37.8 / 36.9 k; FP16 1536^2 (217 MB) 52.2 / 55.5 k, impact
+// 2400 x 1200 (265 MB) 53.2 / 55.3 k, 1792^2 (295 MB) 56.1 / 55.4 k, impact
+// 2400 x 1500 (331 MB) 54.9 / 54.9 k, impact 2400 x 1600 (353 MB) 54.8 /
+// 54.1 k, 2048^2 (386 MB) 57.3 / 56.5 k.  The 16-bit threshold sits between
+// 265 and 295 MB.
 #ifndef LBM_PREFETCH_L2X10
 #define LBM_PREFETCH_L2X10 15
+#endif
+#ifndef LBM_PREFETCH16_L2X10
+#define LBM_PREFETCH16_L2X10 21
 #endif
 // One TX x TY tile with origin (x0, y0): the body shared by the single-case
 // step kernel and the batched kernel (so both give the same bits).
@@ -872,7 +882,8 @@ static lbm_status create_handle(int nx, int ny, const lbm_params* p, void* ws, l
         int l2 = 0;
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device);
         const double bytes = (st16 ? 92.0 : 160.0) * (double)nx * ny;
-        if (bytes * 10.0 < (double)LBM_PREFETCH_L2X10 * l2) h->pf_ahead = 0;
+        const int thr = st16 ? LBM_PREFETCH16_L2X10 : LBM_PREFETCH_L2X10;
+        if (bytes * 10.0 < (double)thr * l2) h->pf_ahead = 0;
     }
     if (e != cudaSuccess) {
         fprintf(stderr, "lbm_create: %s\n", cudaGetErrorString(e));
@@ -1716,8 +1727,10 @@ lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** ou
         int sms = 0, l2 = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess &&
             cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device) == cudaSuccess) {
-            const double bytes = (b->storage == LBM_STORE_FP32 ? 160.0 : 92.0) * (double)b->node_count;
-            if (bytes * 10.0 >= (double)LBM_PREFETCH_L2X10 * l2) b->pf_ahead = LBM_BATCH_PF_PER10SM * sms / 10;
+            const bool st16 = b->storage != LBM_STORE_FP32;
+            const double bytes = (st16 ? 92.0 : 160.0) * (double)b->node_count;
+            const int thr = st16 ? LBM_PREFETCH16_L2X10 : LBM_PREFETCH_L2X10;
+            if (bytes * 10.0 >= (double)thr * l2) b->pf_ahead = LBM_BATCH_PF_PER10SM * sms / 10;
         }
     }
     // batch index of each class slot, for gathering the cases' flags
