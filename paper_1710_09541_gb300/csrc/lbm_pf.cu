@@ -79,9 +79,16 @@ __device__ __forceinline__ bool nbr_in_range(const Nbr& q, int nx, int ny) {
 #ifndef LBM_PREFETCH_PER10SM
 #define LBM_PREFETCH_PER10SM 20
 #endif
-// prefetch distance of the 16-bit step kernels, in tiles per 10 SMs
+// prefetch distance of the 16-bit step kernels, in tiles per 10 SMs: periodic
+// and walled grids.  Measured with one grid per process (FP16 MLUPS at 10 /
+// 15 / 20 / 30 / 40): 2048^2 56.3 / 57.0 / 57.2 / 56.3 / 55.4 k, 3072^2 59.5 /
+// 60.8 / 61.0 / 60.7 / 59.4 k, 1792^2 54.9 / 55.7 / 56.1 / 55.6 / 54.5 k;
+// impact 2400 x 2400 55.6 / 55.6 / 55.2 / 53.6 / 52.3 k
 #ifndef LBM_PREFETCH16_PER10SM
 #define LBM_PREFETCH16_PER10SM 20
+#endif
+#ifndef LBM_PREFETCH16_WALLS_PER10SM
+#define LBM_PREFETCH16_WALLS_PER10SM 15
 #endif
 // prefetch with 16-bit storage too.  With one node per thread the requests
 // cost more than they hid (FP16 at 2048^2 47.6 k -> 45.5 k MLUPS); with two
@@ -873,7 +880,8 @@ static lbm_status create_handle(int nx, int ny, const lbm_params* p, void* ws, l
     int sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     const bool st16 = p->storage != LBM_STORE_FP32;
-    h->pf_ahead = (st16 ? LBM_PREFETCH16_PER10SM : LBM_PREFETCH_PER10SM) * sms / 10;
+    h->pf_ahead = (st16 ? (p->bc_y != LBM_BC_PERIODIC ? LBM_PREFETCH16_WALLS_PER10SM : LBM_PREFETCH16_PER10SM)
+                        : LBM_PREFETCH_PER10SM) * sms / 10;
     {
         // The prefetch pays only when a step's traffic does not fit in L2:
         // below, the rows it asks for are mostly there already and the requests
