@@ -71,13 +71,15 @@ __device__ __forceinline__ bool nbr_in_range(const Nbr& q, int nx, int ny) {
 #ifndef LBM_EARLY_PHIU
 #define LBM_EARLY_PHIU 1
 #endif
-// L2 prefetch distance of the step kernel in tiles, per 10 SMs (0: off);
-// 20 = 2 tiles of 32 x 4 per SM, about a fifth of a resident wave at 10
-// blocks/SM.  Measured at 2, 2.5, 3, 3.5 tiles per SM: 38.97 / 39.00 / 38.80 /
-// 38.65 k MLUPS at 2048^2 and 33.1 / 32.6 / 32.0 / 31.8 k on the 2400 x 600
-// walled impact.
+// L2 prefetch distance of the FP32 step kernel in tiles, per 10 SMs (0: off);
+// 30 = 3 tiles of 32 x 4 per SM, about a third of a resident wave at 10
+// blocks/SM.  With the alternating tile order, one grid per process (MLUPS at
+// 1 / 1.5 / 2 / 3 / 4 / 5 tiles per SM): 2048^2 39.7 / 40.3 / 40.6 / 40.7 /
+// 40.3 / 39.9 k, impact 2400 x 2400 38.6 / 39.2 / 39.7 / 39.9 / 39.6 / 39.3 k,
+// impact 2400 x 600 37.1 / 37.5 / 37.7-37.8 / 37.7 / 37.5 / 37.2 k.  (Before
+// that order, in one process over several grids, 2 to 2.5 had been best.)
 #ifndef LBM_PREFETCH_PER10SM
-#define LBM_PREFETCH_PER10SM 20
+#define LBM_PREFETCH_PER10SM 30
 #endif
 // prefetch distance of the 16-bit step kernels, in tiles per 10 SMs: periodic
 // and walled grids.  Measured with one grid per process (FP16 MLUPS at 10 /
