@@ -162,15 +162,16 @@ __device__ __forceinline__ unsigned int lowbias32(unsigned int x) {
     x ^= x >> 16;
     return x;
 }
-// v rounded to BF16 (its upper 16 bits) with the dither r in [0, 2^16):
-// adding r to the discarded half carries into the kept half with probability
-// (discarded half) / 2^16.  Inf and NaN are truncated without dither, so they
-// stay Inf and NaN (a dither could carry a NaN's all-ones pattern into the
-// sign bit).
-__device__ __forceinline__ unsigned int bf16_sr_bits(float v, unsigned int r) {
-    const unsigned int b = __float_as_uint(v);
-    const unsigned int d = (b & 0x7fffffffu) < 0x7f800000u ? r : 0u;
-    return (b + d) >> 16;
+// (hi, lo) rounded stochastically to a BF16 pair, hi in the upper half: the
+// conversion with random bits (cvt.rs), which adds r[31:16] to the discarded
+// half of hi and r[15:0] to that of lo and truncates, so each carries into
+// the kept half with probability (discarded half) / 2^16.  (Checked on GB300
+// against that integer definition on 2^20 random finite pairs: equal bit for
+// bit.)
+__device__ __forceinline__ unsigned int bf16x2_sr(float hi, float lo, unsigned int r) {
+    unsigned int d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    return d;
 }
 
 // The 16-bit formats store codes: h_i = f_i / w_i - 1/2 for the moving f_i
@@ -252,28 +253,35 @@ struct Shifted16 {
         static_assert(!SR || C::GS == 1.f, "stochastic rounding is a BF16 format");
         unsigned int* P = pw(fb, N);
         float d[9];
-        unsigned int base = 0, r = 0;
-        if constexpr (SR) base = lowbias32((unsigned int)idx ^ seed);
+        if constexpr (SR) {
+            const unsigned int base = lowbias32((unsigned int)idx ^ seed);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            unsigned int w;
-            if constexpr (SR) {
-                // directions 2j - 1 and 2j take the halves of product j
-                if (i & 1) r = (base + (unsigned int)(i >> 1) * 0x9e3779b9u) * 0x85ebca6bu;
-                const unsigned int ri = (i & 1) ? (r >> 16) : (r & 0xffffu);
-                w = (unsigned int)C::from_f(h[i]) | (bf16_sr_bits(k[i], ri) << 16);
-            } else {
-                w = C::pack(h[i], k[i]);
+            for (int i = 1; i < 9; i += 2) {
+                // directions i and i + 1 take the upper and lower halves of
+                // product (i - 1) / 2: one conversion rounds both g codes, one
+                // packs both f codes, and two byte permutations make the words
+                const unsigned int r = (base + (unsigned int)(i >> 1) * 0x9e3779b9u) * 0x85ebca6bu;
+                const unsigned int kk = bf16x2_sr(k[i], k[i + 1], r);
+                const unsigned int hh = C::pack(h[i], h[i + 1]);
+                const unsigned int wi = __byte_perm(hh, kk, 0x7610);
+                const unsigned int wj = __byte_perm(hh, kk, 0x5432);
+                P[(i - 1) * N + idx] = wi;
+                P[i * N + idx] = wj;
+                d[i] = C::to_f(lo(wi));
+                d[i + 1] = C::to_f(lo(wj));
             }
-            P[(i - 1) * N + idx] = w;
-            d[i] = C::to_f(lo(w));
+            static_cast<unsigned short*>(gb)[idx] =
+                (unsigned short)(bf16x2_sr(k[0], 0.f, (base + 4u * 0x9e3779b9u) * 0x85ebca6bu) >> 16);
+        } else {
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const unsigned int w = C::pack(h[i], k[i]);
+                P[(i - 1) * N + idx] = w;
+                d[i] = C::to_f(lo(w));
+            }
+            static_cast<unsigned short*>(gb)[idx] = C::from_f(k[0]);
         }
         static_cast<float*>(fb)[idx] = sub(phi, s8(d));
-        if constexpr (SR)
-            static_cast<unsigned short*>(gb)[idx] =
-                (unsigned short)bf16_sr_bits(k[0], ((base + 4u * 0x9e3779b9u) * 0x85ebca6bu) >> 16);
-        else
-            static_cast<unsigned short*>(gb)[idx] = C::from_f(k[0]);
     }
     // one entry (checkpoint and initial-state permutations)
     __device__ static void putf(void* fb, int N, int i, int idx, float v) {
