@@ -270,6 +270,7 @@ struct Shifted16 {
                 d[i] = C::to_f(lo(wi));
                 d[i + 1] = C::to_f(lo(wj));
             }
+            static_cast<float*>(fb)[idx] = sub(phi, s8(d));
             static_cast<unsigned short*>(gb)[idx] =
                 (unsigned short)(bf16x2_sr(k[0], 0.f, (base + 4u * 0x9e3779b9u) * 0x85ebca6bu) >> 16);
         } else {
@@ -279,9 +280,9 @@ struct Shifted16 {
                 P[(i - 1) * N + idx] = w;
                 d[i] = C::to_f(lo(w));
             }
+            static_cast<float*>(fb)[idx] = sub(phi, s8(d));
             static_cast<unsigned short*>(gb)[idx] = C::from_f(k[0]);
         }
-        static_cast<float*>(fb)[idx] = sub(phi, s8(d));
     }
     // one entry (checkpoint and initial-state permutations)
     __device__ static void putf(void* fb, int N, int i, int idx, float v) {
