@@ -264,20 +264,20 @@ def test_bf16_sr_unbiased(lbm, name):
     """One step from one representable state, taken SR_SAMPLES times with
     BF16_SHIFTED_SR (each step of the handle has its own dithers): every
     stored g code lies within one BF16 spacing of the unrounded value (the
-    same step with FP32 storage), the samples differ, and their mean
-    converges on it (per element the mean's error is p(1 - p) / K in
-    variance, RMS sqrt(1/(6K)) = 0.051 spacings for a uniform fraction p;
-    rounding to nearest would leave a fixed error of RMS 0.29).  The f codes
-    and (phi u) are BF16_SHIFTED's, bit for bit."""
+    oracle's FP64 step from the same state, plus the FP32 allowance of the
+    parity tests), the samples differ, and their mean converges on it (per
+    element the mean's error is p(1 - p) / K in variance, RMS sqrt(1/(6K)) =
+    0.051 spacings for a uniform fraction p; rounding to nearest would leave
+    a fixed error of RMS 0.29).  The f codes and (phi u) are BF16_SHIFTED's,
+    bit for bit."""
     nx, ny, P, init, t0 = CASES[name]
     st = oracle.Lattice(nx, ny, **P).init(init()).step(t0).get_state()
-    with lbm.Lattice(nx, ny, storage=3, **P) as g, lbm.Lattice(nx, ny, storage=0, **P) as e, \
-            lbm.Lattice(nx, ny, storage=2, **P) as rn:
+    with lbm.Lattice(nx, ny, storage=3, **P) as g, lbm.Lattice(nx, ny, storage=2, **P) as rn:
         g.set_state(*(a.astype(np.float32) for a in st))
         rep = g.get_state()
-        e.set_state(*rep)
-        e.step(1)
-        ge = e.get_state()[1].astype(np.float64)
+        o = oracle.Lattice(nx, ny, **P).set_state(*(a.astype(np.float64) for a in rep))
+        o.step(1)
+        ge = o.get_state()[1]
         rn.set_state(*rep)
         rn.step(1)
         rf, rg, ru = rn.get_state()
