@@ -118,6 +118,13 @@ __device__ __forceinline__ bool nbr_in_range(const Nbr& q, int nx, int ny) {
 #ifndef LBM_PREFETCH16_L2X10
 #define LBM_PREFETCH16_L2X10 21
 #endif
+// the same threshold for 16-bit steps that prefetch through tensor maps, whose
+// requests cost almost no issue slots (one grid per process, FP16 MLUPS,
+// prefetch on / off): impact 2400 x 600 (133 MB) 54.8 / 56.0 k, 1536^2
+// (217 MB) 55.2 / 55.1 k, impact 2400 x 1200 (265 MB) 56.3 / 54.6 k
+#ifndef LBM_PREFETCH16_TMA_L2X10
+#define LBM_PREFETCH16_TMA_L2X10 15
+#endif
 // One TX x TY tile with origin (x0, y0): the body shared by the single-case
 // step kernel and the batched kernel (so both give the same bits).
 template <int TX, int TY, bool FIELDS, int WALLS, int ST, bool CHK>
@@ -1010,10 +1017,15 @@ static lbm_status create_handle(int nx, int ny, const lbm_params* p, void* ws, l
         int l2 = 0;
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device);
         const double bytes = (st16 ? 92.0 : 160.0) * (double)nx * ny;
-        const int thr = st16 ? LBM_PREFETCH16_L2X10 : LBM_PREFETCH_L2X10;
+        const bool maps16 = st16 && LBM_TMA_PREFETCH && nx % 8 == 0;  // tensor maps likely
+        const int thr = !st16 ? LBM_PREFETCH_L2X10 : maps16 ? LBM_PREFETCH16_TMA_L2X10 : LBM_PREFETCH16_L2X10;
         if (bytes * 10.0 < (double)thr * l2) h->pf_ahead = 0;
+        if (e == cudaSuccess && h->pf_ahead > 0) {
+            encode_pf_maps(h);
+            // no maps after all: the per-thread requests' own threshold
+            if (st16 && !h->pm[0].on && bytes * 10.0 < (double)LBM_PREFETCH16_L2X10 * l2) h->pf_ahead = 0;
+        }
     }
-    if (e == cudaSuccess && h->pf_ahead > 0) encode_pf_maps(h);
     if (e != cudaSuccess) {
         fprintf(stderr, "lbm_create: %s\n", cudaGetErrorString(e));
         release(h);
