@@ -930,10 +930,8 @@ extern "C" {
 // nx % 8 == 0 covers the 2-byte g_0 plane; plane pitch likewise; the box
 // inside the grid); otherwise, or if the driver lacks the encoder, the step
 // keeps its per-thread prefetch requests.
-static void encode_pf_maps(lbm_handle* h) {
-    h->pm[0].on = h->pm[1].on = 0;
-    if (!LBM_TMA_PREFETCH) return;
-    if (h->prm.storage == LBM_STORE_FP32 && !LBM_TMA_PREFETCH32) return;
+// cuTensorMapEncodeTiled of the driver, or nullptr
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -944,34 +942,68 @@ static void encode_pf_maps(lbm_handle* h) {
             q == cudaDriverEntryPointSuccess)
             enc = (PFN_cuTensorMapEncodeTiled_v12000)f;
     });
-    if (!enc) return;
+    return enc;
+}
+
+// A prefetch map over `planes` planes of nx x ny elements of es bytes at
+// base (one plane: a 2-D map), with a box of bx x by elements and every plane.
+// The caller guarantees nx % 8 == 0 (row and plane pitches multiples of 16
+// bytes) and a 16-byte aligned base.
+static bool encode_prefetch_map(CUtensorMap* m, CUtensorMapDataType t, int es, void* base,
+                                int planes, int nx, int ny, int bx, int by) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t N = (cuuint64_t)nx * ny;
+    const cuuint32_t rank = planes > 1 ? 3 : 2;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * es, N * es};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)planes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, t, rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The four 16-bit prefetch maps of buffer c of handle h (word planes, f_0,
+// g_0, (phi u)), box bx x by
+static bool encode_maps16(const lbm_handle* h, int c, CUtensorMap m[4], int bx, int by) {
+    const int nx = h->nx, ny = h->ny;
+    const size_t N = h->N;
+    return encode_prefetch_map(&m[0], CU_TENSOR_MAP_DATA_TYPE_UINT32, 4,
+                               static_cast<char*>((void*)h->f[c]) + 4 * N, 8, nx, ny, bx, by) &&
+           encode_prefetch_map(&m[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->f[c], 1, nx, ny, bx, by) &&
+           encode_prefetch_map(&m[2], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, h->g[c], 1, nx, ny, bx, by) &&
+           encode_prefetch_map(&m[3], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->phiu, 2, nx, ny, bx, by);
+}
+
+static void encode_pf_maps(lbm_handle* h) {
+    h->pm[0].on = h->pm[1].on = 0;
+    if (!LBM_TMA_PREFETCH) return;
+    if (h->prm.storage == LBM_STORE_FP32 && !LBM_TMA_PREFETCH32) return;
     const bool st16 = h->prm.storage != LBM_STORE_FP32;
     const int tx = st16 ? STEP16_TX : STEP_TX;
     const int th = st16 ? STEP_TY * LBM_NPT16 : STEP_TY;
     const int nx = h->nx, ny = h->ny;
     if (nx % 8 != 0 || nx < tx || ny < th + 2) return;
-    const cuuint64_t N = (cuuint64_t)nx * ny;
-    auto make = [&](CUtensorMap* m, CUtensorMapDataType t, int es, void* base, int planes) {
-        const cuuint32_t rank = planes > 1 ? 3 : 2;
-        const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)planes};
-        const cuuint64_t strides[2] = {(cuuint64_t)nx * es, N * es};
-        const cuuint32_t box[3] = {(cuuint32_t)tx, (cuuint32_t)(th + 2), (cuuint32_t)planes};
-        const cuuint32_t estr[3] = {1, 1, 1};
-        return enc(m, t, rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-    };
     for (int c = 0; c < 2; ++c) {
         PfMaps& pm = h->pm[c];
-        bool ok = make(&pm.phiu, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->phiu, 2);
+        bool ok;
         if (st16) {
-            ok = ok && make(&pm.pop[0], CU_TENSOR_MAP_DATA_TYPE_UINT32, 4,
-                            static_cast<char*>((void*)h->f[c]) + 4 * N, 8);
-            ok = ok && make(&pm.pop[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->f[c], 1);
-            ok = ok && make(&pm.pop[2], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, h->g[c], 1);
+            CUtensorMap m[4];
+            ok = encode_maps16(h, c, m, tx, th + 2);
+            if (ok) {
+                pm.pop[0] = m[0];
+                pm.pop[1] = m[1];
+                pm.pop[2] = m[2];
+                pm.phiu = m[3];
+            }
         } else {
-            ok = ok && make(&pm.pop[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->f[c], 9);
-            ok = ok && make(&pm.pop[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->g[c], 9);
+            ok = encode_prefetch_map(&pm.pop[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->f[c], 9, nx, ny,
+                                     tx, th + 2) &&
+                 encode_prefetch_map(&pm.pop[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->g[c], 9, nx, ny,
+                                     tx, th + 2) &&
+                 encode_prefetch_map(&pm.phiu, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->phiu, 2, nx, ny,
+                                     tx, th + 2);
         }
         if (!ok) {
             h->pm[0].on = h->pm[1].on = 0;
@@ -1407,15 +1439,18 @@ struct CaseDesc {
     float* phiu;
     unsigned int* flag;
     int nx, ny;
-    int cur;  // buffer holding the current state when the batch parity is 0
-    int pad;
+    int cur;   // buffer holding the current state when the batch parity is 0
+    int map0;  // first of the case's 8 prefetch maps in BatchTable::maps (4 per buffer)
     Model m;
 };
 
 // The whole case table travels as a kernel parameter (constant bank): the
 // block-uniform case data then needs no registers of the tile body.
 constexpr int BATCH_MAX_CASES = 200;
+// the box of the batched 16-bit kernels' prefetch maps (x, rows)
+constexpr int BATCH_PF_BOX_X = 32, BATCH_PF_BOX_Y = 10;
 struct BatchTable {
+    const CUtensorMap* maps;  // 16-bit prefetch maps in device memory (nullptr: per-thread requests)
     int ncases;
     int tiles_x[BATCH_MAX_CASES];
     int tile0[BATCH_MAX_CASES + 1];  // first tile of each case; tile0[ncases] = total
@@ -1467,8 +1502,28 @@ __global__ void __launch_bounds__(TX* TY, (ST == ST_FP32 ? LBM_BATCH_THREADS : L
         const int2 pe = __ldg(tiles + (rev ? slot - pf_ahead : slot + pf_ahead));
         const CaseDesc& pc = T.c[pe.x < T.ncases ? pe.x : 0];
         const int pcur = (pc.cur + parity) & 1;
-        prefetch_tile<TX, TH, TX * TY, ST>(pc.f[pcur], pc.g[pcur], pc.phiu, pc.nx, pc.ny, WALLS,
-                                           pe.y & 0xffff, pe.y >> 16);
+        if (ST != ST_FP32 && T.maps != nullptr) {
+            // through the case's tensor maps, boxes of 32 x 10 elements:
+            // (TX / 32) x ceil((TH + 2) / 10) boxes per map, one box of one
+            // map per thread (as in the single-case 16-bit step)
+            constexpr int SX = TX / BATCH_PF_BOX_X;
+            constexpr int SY = (TH + 2 + BATCH_PF_BOX_Y - 1) / BATCH_PF_BOX_Y;
+            const int t = threadIdx.y * TX + threadIdx.x;
+            if (t < 4 * SX * SY) {
+                const int k = t & 3, sub = t >> 2;
+                const int x = (pe.y & 0xffff) * TX + BATCH_PF_BOX_X * (sub % SX);
+                const int r0 = (pe.y >> 16) * TH;
+                const int y = (r0 > 0 ? r0 - 1 : 0) + BATCH_PF_BOX_Y * (sub / SX);
+                const CUtensorMap* mp = T.maps + pc.map0 + 4 * pcur + k;
+                if (k == 1 || k == 2)
+                    tma_prefetch_2d(mp, x, y);
+                else
+                    tma_prefetch_3d(mp, x, y, 0);
+            }
+        } else {
+            prefetch_tile<TX, TH, TX * TY, ST>(pc.f[pcur], pc.g[pcur], pc.phiu, pc.nx, pc.ny, WALLS,
+                                               pe.y & 0xffff, pe.y >> 16);
+        }
     }
     const int2 e = __ldg(tiles + slot);
 #if LBM_DEBUG_CHECKS
@@ -1564,6 +1619,7 @@ struct lbm_batch {
     unsigned int* d_flags = nullptr;    // gathered flags, one per case
     int cand[BATCH_NCLASS] = {1, 1};  // tile shape in use per class (index into BATCH_TX/TY)
     int pf_ahead = 0;                 // L2 prefetch distance in tiles (0: off)
+    CUtensorMap* d_maps = nullptr;    // the 16-bit prefetch maps, 8 per case (nullptr: none)
     bool tuned = false;
     double tuned_us[BATCH_NCLASS][BATCH_NCAND] = {};
     cudaGraphExec_t graph = nullptr;
@@ -1599,6 +1655,7 @@ static void batch_release(lbm_batch* b) {
     for (int* t : b->d_slot)
         if (t) cudaFree(t);
     if (b->d_flags) cudaFree(b->d_flags);
+    if (b->d_maps) cudaFree(b->d_maps);
     for (cudaEvent_t e : {b->ev_in, b->ev_out, b->ev_fork, b->ev_join, b->t0, b->t1})
         if (e) cudaEventDestroy(e);
     for (int k = 0; k < BATCH_NCLASS; ++k)
@@ -1826,6 +1883,7 @@ lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** ou
                 d.nx = h->nx;
                 d.ny = h->ny;
                 d.cur = h->cur;
+                d.map0 = -1;
                 d.m = h->model;
                 T.tiles_x[j] = (h->nx + BATCH_TX[k] - 1) / BATCH_TX[k];
                 T.tile0[j] = (int)tiles;
@@ -1869,9 +1927,36 @@ lbm_status lbm_batch_create(int ncases, lbm_handle* const* cases, lbm_batch** ou
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) == cudaSuccess &&
             cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device) == cudaSuccess) {
             const bool st16 = b->storage != LBM_STORE_FP32;
+            bool maps16 = st16 && LBM_TMA_PREFETCH && tensor_map_encoder() != nullptr;
+            for (int c = 0; c < ncases; ++c)
+                maps16 = maps16 && cases[c]->nx % 8 == 0 && cases[c]->nx >= BATCH_PF_BOX_X &&
+                         cases[c]->ny >= BATCH_PF_BOX_Y;
             const double bytes = (st16 ? 92.0 : 160.0) * (double)b->node_count;
-            const int thr = st16 ? LBM_PREFETCH16_L2X10 : LBM_PREFETCH_L2X10;
+            const int thr = !st16 ? LBM_PREFETCH_L2X10 : maps16 ? LBM_PREFETCH16_TMA_L2X10 : LBM_PREFETCH16_L2X10;
             if (bytes * 10.0 >= (double)thr * l2) b->pf_ahead = LBM_BATCH_PF_PER10SM * sms / 10;
+            // 16-bit batches prefetch through tensor maps: 8 per case (4 per
+            // buffer), in device memory, indexed from the case table
+            if (b->pf_ahead > 0 && maps16) {
+                std::vector<CUtensorMap> maps((size_t)ncases * 8);
+                bool ok = true;
+                for (int c = 0; c < ncases && ok; ++c)
+                    ok = encode_maps16(cases[c], 0, &maps[8 * c], BATCH_PF_BOX_X, BATCH_PF_BOX_Y) &&
+                         encode_maps16(cases[c], 1, &maps[8 * c + 4], BATCH_PF_BOX_X, BATCH_PF_BOX_Y);
+                if (ok && cudaMalloc(&b->d_maps, maps.size() * sizeof(CUtensorMap)) == cudaSuccess &&
+                    cudaMemcpy(b->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
+                               cudaMemcpyHostToDevice) == cudaSuccess) {
+                    for (int cls = 0; cls < BATCH_NCLASS; ++cls)
+                        for (int k = 0; k < BATCH_NCAND; ++k) b->tab(cls, k).maps = b->d_maps;
+                    for (int c = 0; c < ncases; ++c)
+                        for (int k = 0; k < BATCH_NCAND; ++k)
+                            b->tab(b->cls_of[c], k).c[b->slot_of[c]].map0 = 8 * c;
+                } else {
+                    if (b->d_maps) cudaFree(b->d_maps);
+                    b->d_maps = nullptr;
+                    // the per-thread requests' own threshold
+                    if (bytes * 10.0 < (double)LBM_PREFETCH16_L2X10 * l2) b->pf_ahead = 0;
+                }
+            }
         }
     }
     // batch index of each class slot, for gathering the cases' flags
