@@ -85,7 +85,10 @@ __device__ __forceinline__ bool nbr_in_range(const Nbr& q, int nx, int ny) {
 // and walled grids.  Measured with one grid per process (FP16 MLUPS at 10 /
 // 15 / 20 / 30 / 40): 2048^2 56.3 / 57.0 / 57.2 / 56.3 / 55.4 k, 3072^2 59.5 /
 // 60.8 / 61.0 / 60.7 / 59.4 k, 1792^2 54.9 / 55.7 / 56.1 / 55.6 / 54.5 k;
-// impact 2400 x 2400 55.6 / 55.6 / 55.2 / 53.6 / 52.3 k
+// impact 2400 x 2400 55.6 / 55.6 / 55.2 / 53.6 / 52.3 k (per-thread requests).
+// With the tensor-map prefetch, at 10 / 20 / 30 (walls 10 / 15 / 30): 2048^2
+// 59.8 / 60.7 / 60.6 k, 3072^2 62.8 / 64.3 / 64.7 k, impact 2400 x 2400
+// 58.5 / 58.7 / 56.8 k
 #ifndef LBM_PREFETCH16_PER10SM
 #define LBM_PREFETCH16_PER10SM 20
 #endif
