@@ -67,6 +67,38 @@ def test_batch_equals_individual_steps(lbm, storage):
             lat.close()
 
 
+@pytest.mark.parametrize("odd", [False, True])
+def test_large_batch_with_prefetch_equals_individual_steps(lbm, odd):
+    """The 64-case sweep with FP16 storage (16.5 M nodes, 1.5 GB per step,
+    so the batched kernel prefetches the tile two per SM ahead), 10 steps,
+    against four of its cases stepped alone, bit for bit.  Every case of the
+    sweep has nx % 8 == 0, and the prefetch goes through the cases' tensor
+    maps; with one more case of nx = 1004 the whole batch falls back to
+    per-thread prefetch requests.  Small batches, as in the other tests, run
+    without the prefetch."""
+    specs = cases.batch_cases()
+    pick = [0, 1, 36, 63]
+    if odd:
+        P = cases.params_static_drop(ratio=100.0)
+        phi0 = cases.drop(1004, 300, 40.0, P["W"])
+        specs = specs + [dict(nx=1004, ny=300, kind="static_drop", params=P, phi0=phi0,
+                              ux0=np.zeros_like(phi0), uy0=np.zeros_like(phi0))]
+        pick.append(64)
+    A = _lattices(lbm, specs, 1)
+    B = _lattices(lbm, [specs[k] for k in pick], 1)
+    try:
+        with lbm.Batch(A) as bt:
+            bt.step(10)
+        for lat in B:
+            lat.step(10)
+        for k, b in zip(pick, B):
+            for x, y in zip(A[k].get_state(), b.get_state()):
+                assert np.array_equal(x, y), k
+    finally:
+        for lat in A + B:
+            lat.close()
+
+
 @pytest.mark.parametrize("kinds", ["static_drop", "impact"])
 def test_batch_of_one_class(lbm, kinds):
     """All cases in one boundary class (the other class empty), an odd step
